@@ -1,0 +1,158 @@
+/*
+ * bblock.h -- C ABI of the GB300 (sm_103a) stochastic-LapH baryon-block library.
+ *
+ * What it computes (arXiv:2211.16278, Sec. 2): for each time slice t and each
+ * momentum p,
+ *
+ *   q_i[alpha][x][a][d] = sum_l V[l][x][a] * phi_i[alpha*n_ev + l][d]            (Eq. 2)
+ *   B[t][p][d1][d2][d3] = sum_s c_s^{(p)} sum_x e^{-i p.x} eps_{abc}
+ *                         q1[alpha_s][x][a][d1] q2[beta_s][x][b][d2] q3[gamma_s][x][c][d3]
+ *                                                                                  (Eq. 1/3)
+ *
+ * with p = 2 pi n / L for integer triples n, sites x = x0 + L*(x1 + L*x2) in
+ * [0, L)^3, eps_{012} = +1 and no complex conjugation. The spin sum over
+ * (alpha_s, beta_s, gamma_s, c_s) is the caller-supplied baryon operator of
+ * Eq. (1); with a single triple and c = 1 the call is the kernel of Eq. (3).
+ *
+ * Complex numbers are interleaved (re, im) IEEE doubles ("complex128").
+ * Arrays are dense, row-major, with the last index fastest:
+ *   V      complex128 [n_t][n_ev][L^3][3]            eigenvector l, site x, colour a
+ *   phi_i  complex128 [n_t][4*n_ev][nd_i]            row alpha*n_ev + l, column d
+ *   B_out  complex128 [n_t][n_mom][nd1][nd2][nd3]
+ *   momenta     int32 [n_mom][3]                     host memory, any sign
+ *   spin_idx    int32 [n_spin][3]                    host memory, entries in 0..3
+ *   spin_coeffs complex128 [n_spin] (coeff_per_mom == 0) or [n_mom][n_spin] (!= 0), host memory
+ *
+ * Ownership: the caller owns every argument buffer; the library never frees
+ * them and keeps no pointer to them after a call returns. A context owns its
+ * device workspace (reconstructed fields, phase table, per-slab partial sums)
+ * and the host staging buffers of bblock_compute_host; bblock_destroy releases
+ * them. A context is not thread-safe; use one context per host thread and
+ * stream, or serialise calls.
+ *
+ * Errors: every int-returning entry point returns BBLOCK_OK (0) or one of the
+ * negative codes below and never throws. bblock_last_error() gives a one-line
+ * message. Kernel launches are asynchronous: errors the device detects show up
+ * in bblock_status(), which synchronises the stream of the last call.
+ */
+#ifndef BBLOCK_H
+#define BBLOCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BBLOCK_OK 0
+#define BBLOCK_ERR_INVALID_ARG (-1)  /* bad size, index, pointer kind or alignment */
+#define BBLOCK_ERR_UNSUPPORTED (-2)  /* valid request this build does not implement */
+#define BBLOCK_ERR_OOM (-3)          /* device or pinned-host allocation failed */
+#define BBLOCK_ERR_CUDA (-4)         /* a CUDA runtime call failed */
+#define BBLOCK_ERR_TIMEOUT (-5)      /* a bounded device wait gave up */
+#define BBLOCK_ERR_DEVICE_FLAG (-6)  /* a kernel flagged an inconsistent job table */
+
+/* Arithmetic of the projection and the contraction. */
+typedef enum {
+  BBLOCK_FP64 = 0,       /* IEEE double throughout (DFMA); parity target 1e-12 */
+  BBLOCK_TF32X3 = 1,     /* tensor-core TF32 split (hi/lo, 3 products), FP32 accumulate */
+  BBLOCK_BF16_SPLIT = 2  /* tensor-core BF16 split (3, 6 or 9 products), FP32 accumulate */
+} bblock_precision;
+
+typedef struct bblock_ctx bblock_ctx;
+
+typedef struct {
+  int L;             /* lattice extent; X = L^3 sites per time slice; 1 <= L <= 128 */
+  int n_ev;          /* Laplacian eigenvectors; 1 <= n_ev <= 3 L^3 */
+  int max_ndil;      /* bound on every nd_i passed later; 1 <= max_ndil <= 256 */
+  int precision;     /* a bblock_precision value */
+  int bf16_products; /* BBLOCK_BF16_SPLIT: 3, 6 or 9 split products; ignored otherwise */
+  int device;        /* CUDA device ordinal the context runs on */
+} bblock_config;
+
+/* Create a context for one device. *out is set on success, NULL otherwise.
+ * No device memory is reserved until the first compute call. */
+int bblock_create(bblock_ctx** out, const bblock_config* cfg);
+
+/* Release the context and everything it owns. Waits for its pending work. NULL is a no-op. */
+void bblock_destroy(bblock_ctx* ctx);
+
+/* One-line description of the last error on this context ("" if none). Valid until the next call. */
+const char* bblock_last_error(const bblock_ctx* ctx);
+
+/* Synchronise the stream of the last call and report device-side status:
+ * BBLOCK_OK, BBLOCK_ERR_CUDA (a launch or kernel failed) or BBLOCK_ERR_DEVICE_FLAG. */
+int bblock_status(bblock_ctx* ctx);
+
+/* Baryon blocks of n_t time slices and one noise triple (Eq. 2 then Eq. 1).
+ *   V, phi1, phi2, phi3, B_out: DEVICE pointers (cudaMalloc or managed), 16-byte aligned,
+ *     layouts as in the file comment; V and phi_i hold n_t consecutive time slices.
+ *   nd1, nd2, nd3: dilution sizes, 1..max_ndil.
+ *   n_mom >= 0 momenta (n_mom == 0 or n_t == 0 is a no-op); n_spin >= 1 spin triples.
+ *   coeff_per_mom: 0 -> spin_coeffs is [n_spin]; 1 -> [n_mom][n_spin] (Eq. 1's c depends on p).
+ *   stream: a cudaStream_t (NULL = legacy default stream). Work is enqueued, not awaited.
+ * The momentum phases are cached in the context per (L, momentum list). */
+int bblock_compute(bblock_ctx* ctx, int n_t, const void* V, const void* phi1, const void* phi2,
+                   const void* phi3, int nd1, int nd2, int nd3, const int32_t* momenta,
+                   int n_mom, const int32_t* spin_idx, const double* spin_coeffs, int n_spin,
+                   int coeff_per_mom, void* B_out, void* stream);
+
+/* Same computation from HOST buffers: copies V and phi_i to context-owned device
+ * buffers on `stream`, computes, copies B back into the host buffer B_out and
+ * synchronises the stream before returning. Page-locked host memory
+ * (cudaHostAlloc / pin_memory) gives full copy bandwidth; pageable memory works. */
+int bblock_compute_host(bblock_ctx* ctx, int n_t, const void* V, const void* phi1,
+                        const void* phi2, const void* phi3, int nd1, int nd2, int nd3,
+                        const int32_t* momenta, int n_mom, const int32_t* spin_idx,
+                        const double* spin_coeffs, int n_spin, int coeff_per_mom, void* B_out,
+                        void* stream);
+
+/* One unit of a batched run: one time slice of one noise triple.
+ * All pointers are device pointers with the single-slice layouts above
+ * (V [n_ev][L^3][3], phi_i [4*n_ev][nd_i], B_out [n_mom][nd1][nd2][nd3]). */
+typedef struct {
+  const void* V;
+  const void* phi1;
+  const void* phi2;
+  const void* phi3;
+  int nd1, nd2, nd3;
+  void* B_out;
+} bblock_job;
+
+/* Every job of a run (time slices x noise triples, dilution sizes may differ per
+ * job) in one pass: one projection launch, one persistent contraction launch
+ * and one reduction launch for all jobs, sharing the momenta and spin operator
+ * (Sec. 2: the kernel is called for many noise and spin combinations with the
+ * same momentum set and eigenvectors). Arguments as in bblock_compute. */
+int bblock_compute_batch(bblock_ctx* ctx, const bblock_job* jobs, int n_jobs,
+                         const int32_t* momenta, int n_mom, const int32_t* spin_idx,
+                         const double* spin_coeffs, int n_spin, int coeff_per_mom, void* stream);
+
+/* Device bytes the context holds right now (workspace + caches). */
+size_t bblock_workspace_bytes(const bblock_ctx* ctx);
+
+/* Number of kernel launches enqueued by the last compute call. */
+int bblock_last_launch_count(const bblock_ctx* ctx);
+
+/* Per-kernel timing: while enabled, every launch of the library is bracketed by
+ * two CUDA events recorded on the launching stream. */
+typedef struct {
+  char name[32];    /* "phase", "project", "contract", "reduce", ... */
+  int launches;     /* launches timed since the last read */
+  double total_ms;  /* summed event-to-event durations of those launches */
+} bblock_kernel_stat;
+
+/* Turn launch timing on (enable != 0) or off. Off by default. */
+int bblock_profile_enable(bblock_ctx* ctx, int enable);
+
+/* Synchronise the recorded events, write up to max_entries per-kernel totals to
+ * out (one entry per kernel name that launched), set *n_entries, and reset. */
+int bblock_profile_read(bblock_ctx* ctx, bblock_kernel_stat* out, int max_entries,
+                        int* n_entries);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBLOCK_H */

@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) stochastic-LapH baryon blocks (arXiv:2211.16278).
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in
+``include/bblock.h``); :mod:`.bblock` is its Python binding.
+"""
+from .bblock import (BblockError, Context, bblock_compute, bblock_compute_batch,  # noqa: F401
+                     bblock_compute_host, bblock_create, bblock_destroy, bblock_last_error,
+                     bblock_last_launch_count, bblock_profile_enable,
+                     bblock_profile_read, bblock_status, bblock_workspace_bytes, load)

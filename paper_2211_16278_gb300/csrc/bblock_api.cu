@@ -1,0 +1,672 @@
+// Host side of the C ABI declared in include/bblock.h: argument checks, spin-operator
+// analysis, workspace, phase cache, job tables and the launch sequence
+//   phase table (cached) -> projection (Eq. 2) -> contraction (Eq. 1/3) -> slab reduction.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/bblock.h"
+#include "bblock_internal.h"
+
+using namespace bb;
+
+struct bblock_ctx {
+  bblock_config cfg{};
+  int X = 0, rows = 0, num_sms = 0;
+  std::string err;
+  cudaStream_t last_stream = nullptr;
+  int* d_status = nullptr;
+  // phase cache
+  std::vector<int32_t> phase_mom;
+  double2* d_phase = nullptr;
+  size_t phase_cap = 0;
+  int* d_mom = nullptr;
+  size_t mom_cap = 0;
+  // workspace (fields + partials)
+  char* d_ws = nullptr;
+  size_t ws_cap = 0;
+  // job tables: device copy + pinned host staging guarded by an event
+  char* d_tab = nullptr;
+  size_t tab_cap = 0;
+  char* h_tab = nullptr;
+  size_t h_tab_cap = 0;
+  cudaEvent_t tab_free = nullptr;
+  // device staging for bblock_compute_host
+  char* d_io = nullptr;
+  size_t io_cap = 0;
+  int last_launches = 0;
+  size_t ws_budget = 0;
+  // launch timing (bblock_profile_enable)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Timed { int kind; cudaEvent_t a, b; };
+  std::vector<Timed> timed;
+};
+
+namespace {
+enum KernelKind { K_PHASE = 0, K_PROJECT, K_CONTRACT, K_REDUCE, K_COUNT };
+const char* const kKernelNames[K_COUNT] = {"phase", "project", "contract", "reduce"};
+
+cudaEvent_t take_event(bblock_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+// Enqueue `launch` on `s`; when timing is on, bracket it with events.
+template <class F>
+cudaError_t timed_launch(bblock_ctx* c, int kind, cudaStream_t s, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->prof) {
+    a = take_event(c);
+    b = take_event(c);
+    if (a && b) cudaEventRecord(a, s);
+  }
+  cudaError_t e = launch();
+  c->last_launches++;
+  if (a && b) {
+    cudaEventRecord(b, s);
+    c->timed.push_back({kind, a, b});
+  } else {
+    if (a) c->ev_pool.push_back(a);
+    if (b) c->ev_pool.push_back(b);
+  }
+  return e;
+}
+}  // namespace
+
+namespace {
+
+int fail(bblock_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+int cuda_fail(bblock_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, BBLOCK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                             \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);      \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int grow_device(bblock_ctx* c, char** p, size_t* cap, size_t need) {
+  if (need <= *cap) return BBLOCK_OK;
+  if (*p) {
+    cudaError_t e = cudaStreamSynchronize(c->last_stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize before workspace growth");
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+  }
+  if (cudaMalloc(p, need) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, BBLOCK_ERR_OOM, "cudaMalloc of %zu bytes failed", need);
+  }
+  *cap = need;
+  return BBLOCK_OK;
+}
+
+// Whether `p` is device-accessible memory of the context's device.
+bool is_device_ptr(const bblock_ctx* c, const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == c->cfg.device;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Spin operator of Eq. (1) reduced to what the kernels consume.
+struct SpinPlan {
+  int n1 = 0, n2 = 0;                 // distinct alpha (line 1), beta (line 2)
+  int slot1[4], slot2[4];             // spin -> slot, -1 if unused
+  int alpha_of1[4], beta_of2[4];      // slot -> spin
+  int n_pairs = 0;
+  int a_slot[kMaxPairs], b_slot[kMaxPairs];
+  int pair_alpha[kMaxPairs], pair_beta[kMaxPairs];
+  // terms of each folded line-3 field, per momentum set index (1 if broadcast, P if per-momentum)
+  int n_coef_sets = 1;
+  std::vector<std::vector<std::vector<std::pair<int, double2>>>> terms;  // [set][pair] -> (gamma, c)
+};
+
+int plan_spins(bblock_ctx* c, const int32_t* spin_idx, const double* coeffs, int n_spin,
+               int per_mom, int n_mom, SpinPlan* sp) {
+  for (int i = 0; i < 4; ++i) sp->slot1[i] = sp->slot2[i] = -1;
+  std::vector<int> pair_of(n_spin);
+  for (int s = 0; s < n_spin; ++s) {
+    const int al = spin_idx[3 * s], be = spin_idx[3 * s + 1], ga = spin_idx[3 * s + 2];
+    if (al < 0 || al > 3 || be < 0 || be > 3 || ga < 0 || ga > 3)
+      return fail(c, BBLOCK_ERR_INVALID_ARG, "spin triple %d = (%d,%d,%d) outside 0..3", s, al, be, ga);
+    if (sp->slot1[al] < 0) { sp->alpha_of1[sp->n1] = al; sp->slot1[al] = sp->n1++; }
+    if (sp->slot2[be] < 0) { sp->beta_of2[sp->n2] = be; sp->slot2[be] = sp->n2++; }
+    int pr = -1;
+    for (int k = 0; k < sp->n_pairs; ++k)
+      if (sp->pair_alpha[k] == al && sp->pair_beta[k] == be) pr = k;
+    if (pr < 0) {
+      pr = sp->n_pairs++;
+      sp->pair_alpha[pr] = al;
+      sp->pair_beta[pr] = be;
+      sp->a_slot[pr] = sp->slot1[al];
+      sp->b_slot[pr] = sp->slot2[be];
+    }
+    pair_of[s] = pr;
+  }
+  sp->n_coef_sets = per_mom ? n_mom : 1;
+  sp->terms.assign(sp->n_coef_sets, std::vector<std::vector<std::pair<int, double2>>>(sp->n_pairs));
+  for (int set = 0; set < sp->n_coef_sets; ++set)
+    for (int s = 0; s < n_spin; ++s) {
+      const double* cz = coeffs + 2 * ((size_t)set * n_spin + s);
+      const int ga = spin_idx[3 * s + 2];
+      auto& tl = sp->terms[set][pair_of[s]];
+      bool merged = false;
+      for (auto& t : tl)
+        if (t.first == ga) { t.second.x += cz[0]; t.second.y += cz[1]; merged = true; }
+      if (!merged) tl.push_back({ga, make_double2(cz[0], cz[1])});
+    }
+  return BBLOCK_OK;
+}
+
+int ensure_phase(bblock_ctx* c, const int32_t* momenta, int n_mom, cudaStream_t s) {
+  std::vector<int32_t> key(momenta, momenta + 3 * n_mom);
+  if (c->d_phase && key == c->phase_mom) return BBLOCK_OK;
+  int rc = grow_device(c, reinterpret_cast<char**>(&c->d_phase), &c->phase_cap,
+                       sizeof(double2) * (size_t)c->X * n_mom);
+  if (rc) return rc;
+  rc = grow_device(c, reinterpret_cast<char**>(&c->d_mom), &c->mom_cap, sizeof(int) * 3 * n_mom);
+  if (rc) return rc;
+  CK(c, cudaMemcpyAsync(c->d_mom, momenta, sizeof(int) * 3 * n_mom, cudaMemcpyHostToDevice, s));
+  CK(c, timed_launch(c, K_PHASE, s, [&] { return launch_phase_table(c->cfg.L, n_mom, c->d_mom, c->d_phase, s); }));
+  // the host momentum array may be reused by the caller right after return
+  CK(c, cudaStreamSynchronize(s));
+  c->phase_mom = key;
+  return BBLOCK_OK;
+}
+
+// Copy `bytes` of host tables into the device table buffer on `s` via the pinned staging buffer.
+int upload_tables(bblock_ctx* c, const void* src, size_t bytes, cudaStream_t s) {
+  if (c->tab_free) CK(c, cudaEventSynchronize(c->tab_free));  // previous upload has drained
+  if (bytes > c->h_tab_cap) {
+    if (c->h_tab) cudaFreeHost(c->h_tab);
+    c->h_tab = nullptr;
+    c->h_tab_cap = 0;
+    if (cudaHostAlloc(&c->h_tab, bytes, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, BBLOCK_ERR_OOM, "cudaHostAlloc of %zu bytes failed", bytes);
+    }
+    c->h_tab_cap = bytes;
+  }
+  int rc = grow_device(c, &c->d_tab, &c->tab_cap, bytes);
+  if (rc) return rc;
+  memcpy(c->h_tab, src, bytes);
+  CK(c, cudaMemcpyAsync(c->d_tab, c->h_tab, bytes, cudaMemcpyHostToDevice, s));
+  CK(c, cudaEventRecord(c->tab_free, s));
+  return BBLOCK_OK;
+}
+
+// Pick the slab count so that the work units fill the persistent grid evenly.
+int choose_slabs(long long tiles, int grid, int X, int xc, int max_slabs) {
+  const int s_hi = std::max(1, std::min(max_slabs, (X + xc - 1) / xc));
+  const int s_lo = std::max(1, (int)std::min<long long>(s_hi, (4LL * grid + tiles - 1) / tiles));
+  int best = s_lo;
+  double best_eff = 0.0;
+  for (int s = s_lo; s <= s_hi; ++s) {
+    const long long units = tiles * s;
+    const long long waves = (units + grid - 1) / grid;
+    const double eff = (double)units / (double)(waves * grid);
+    if (eff > best_eff + 1e-9) { best_eff = eff; best = s; }
+    if (eff >= 0.97) break;
+  }
+  return best;
+}
+
+struct JobIn {
+  const double2* V;
+  const double2* phi[3];
+  int nd[3];
+  double2* B;
+};
+
+int validate_common(bblock_ctx* c, const int32_t* momenta, int n_mom, const int32_t* spin_idx,
+                    const double* coeffs, int n_spin, int per_mom) {
+  if (n_mom < 0) return fail(c, BBLOCK_ERR_INVALID_ARG, "n_mom = %d < 0", n_mom);
+  if (n_mom > 0 && !momenta) return fail(c, BBLOCK_ERR_INVALID_ARG, "momenta is NULL");
+  if (n_spin < 1 || n_spin > 64) return fail(c, BBLOCK_ERR_INVALID_ARG, "n_spin = %d outside 1..64", n_spin);
+  if (!spin_idx || !coeffs) return fail(c, BBLOCK_ERR_INVALID_ARG, "spin_idx / spin_coeffs is NULL");
+  if (per_mom != 0 && per_mom != 1) return fail(c, BBLOCK_ERR_INVALID_ARG, "coeff_per_mom must be 0 or 1");
+  return BBLOCK_OK;
+}
+
+int validate_job(bblock_ctx* c, const JobIn& j, int idx, bool device) {
+  const void* ptrs[5] = {j.V, j.phi[0], j.phi[1], j.phi[2], j.B};
+  const char* names[5] = {"V", "phi1", "phi2", "phi3", "B_out"};
+  for (int k = 0; k < 5; ++k) {
+    if (!ptrs[k]) return fail(c, BBLOCK_ERR_INVALID_ARG, "job %d: %s is NULL", idx, names[k]);
+    if (!aligned16(ptrs[k]))
+      return fail(c, BBLOCK_ERR_INVALID_ARG, "job %d: %s is not 16-byte aligned", idx, names[k]);
+    if (device && !is_device_ptr(c, ptrs[k]))
+      return fail(c, BBLOCK_ERR_INVALID_ARG, "job %d: %s is not device memory of device %d", idx,
+                  names[k], c->cfg.device);
+  }
+  for (int i = 0; i < 3; ++i)
+    if (j.nd[i] < 1 || j.nd[i] > c->cfg.max_ndil)
+      return fail(c, BBLOCK_ERR_INVALID_ARG, "job %d: nd%d = %d outside 1..max_ndil (%d)", idx,
+                  i + 1, j.nd[i], c->cfg.max_ndil);
+  return BBLOCK_OK;
+}
+
+// The whole launch sequence for a list of jobs sharing momenta and spin operator.
+int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momenta, int n_mom,
+             const int32_t* spin_idx, const double* coeffs, int n_spin, int per_mom,
+             cudaStream_t s) {
+  c->last_launches = 0;
+  c->last_stream = s;
+  if (jobs.empty() || n_mom == 0) return BBLOCK_OK;
+  CK(c, cudaSetDevice(c->cfg.device));
+  SpinPlan sp;
+  int rc = plan_spins(c, spin_idx, coeffs, n_spin, per_mom, n_mom, &sp);
+  if (rc) return rc;
+  if (sp.n_pairs > kMaxPairs) return fail(c, BBLOCK_ERR_UNSUPPORTED, "more than %d spin pairs", kMaxPairs);
+  if (c->cfg.precision != BBLOCK_FP64)
+    return fail(c, BBLOCK_ERR_UNSUPPORTED, "precision %d is not built yet", c->cfg.precision);
+  rc = ensure_phase(c, momenta, n_mom, s);
+  if (rc) return rc;
+
+  const int X = c->X, rows = c->rows, n_ev = c->cfg.n_ev;
+  const int n3_fields = sp.n_pairs * sp.n_coef_sets;
+  const int P_launch = per_mom ? 1 : std::min(n_mom, kMaxPGroup);
+  const int xc = fp64_sites_per_chunk(sp.n_pairs);
+  const Fp64Tile tl = fp64_tile_for(P_launch);  // one tile shape for every momentum group
+  const int ctas = fp64_contract_ctas_per_sm(P_launch, tl.rn, sp.n_pairs) * c->num_sms;
+  const int max_slabs = 64;
+
+  // bytes per job: fields + partials at the largest slab count
+  auto job_bytes = [&](const JobIn& j, int n_slab) {
+    size_t f = (size_t)rows * (sp.n1 * j.nd[0] + sp.n2 * j.nd[1] + n3_fields * j.nd[2]) * sizeof(double2);
+    size_t p = (size_t)n_slab * n_mom * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(double2);
+    return align_up(f, 256) + align_up(p, 256);
+  };
+
+  size_t job_idx = 0;
+  while (job_idx < jobs.size()) {
+    // wave of jobs whose workspace fits the budget
+    size_t end = job_idx, need = 0;
+    while (end < jobs.size()) {
+      size_t b = job_bytes(jobs[end], max_slabs);
+      if (end > job_idx && need + b > c->ws_budget) break;
+      need += b;
+      ++end;
+    }
+    const int nj = (int)(end - job_idx);
+    long long tiles = 0;
+    int max_nd3 = 0, max_ndf = 0;
+    long long max_elems = 0;
+    for (size_t k = job_idx; k < end; ++k) {
+      const JobIn& j = jobs[k];
+      tiles += (long long)((j.nd[0] * j.nd[1] + 16 * tl.rm - 1) / (16 * tl.rm)) *
+               ((j.nd[2] + 16 * tl.rn - 1) / (16 * tl.rn));
+      max_nd3 = std::max(max_nd3, j.nd[2]);
+      for (int i = 0; i < 3; ++i) max_ndf = std::max(max_ndf, j.nd[i]);
+      max_elems = std::max(max_elems, (long long)n_mom * j.nd[0] * j.nd[1] * j.nd[2]);
+    }
+    int n_slab = choose_slabs(tiles, ctas, X, xc, max_slabs);
+    int sites_per_slab = (X + n_slab - 1) / n_slab;
+    sites_per_slab = (sites_per_slab + xc - 1) / xc * xc;
+    n_slab = (X + sites_per_slab - 1) / sites_per_slab;
+
+    size_t ws_need = 0;
+    for (size_t k = job_idx; k < end; ++k) ws_need += job_bytes(jobs[k], n_slab);
+    rc = grow_device(c, &c->d_ws, &c->ws_cap, ws_need);
+    if (rc) return rc;
+
+    // field and job tables
+    std::vector<ProjField> fields;
+    std::vector<std::vector<ContractJob>> cjobs(sp.n_coef_sets, std::vector<ContractJob>(nj));
+    char* ws = c->d_ws;
+    long long unit = 0;
+    for (int k = 0; k < nj; ++k) {
+      const JobIn& j = jobs[job_idx + k];
+      char* base = ws;
+      auto add_field = [&](const double2* phi, int nd, int n_terms, const int* offs,
+                           const double2* w) -> double2* {
+        ProjField f{};
+        f.V = j.V;
+        f.phi = phi;
+        f.q = reinterpret_cast<double2*>(base);
+        f.nd = nd;
+        f.n_terms = n_terms;
+        for (int t = 0; t < n_terms; ++t) { f.row_off[t] = offs[t]; f.w[t] = w[t]; }
+        base += (size_t)rows * nd * sizeof(double2);
+        fields.push_back(f);
+        return f.q;
+      };
+      const double2 one = make_double2(1.0, 0.0);
+      const double2* q1[4] = {};
+      const double2* q2[4] = {};
+      for (int sl = 0; sl < sp.n1; ++sl) {
+        int off = sp.alpha_of1[sl] * n_ev;
+        q1[sl] = add_field(j.phi[0], j.nd[0], 1, &off, &one);
+      }
+      for (int sl = 0; sl < sp.n2; ++sl) {
+        int off = sp.beta_of2[sl] * n_ev;
+        q2[sl] = add_field(j.phi[1], j.nd[1], 1, &off, &one);
+      }
+      std::vector<std::vector<const double2*>> q3(sp.n_coef_sets, std::vector<const double2*>(sp.n_pairs));
+      for (int set = 0; set < sp.n_coef_sets; ++set)
+        for (int pr = 0; pr < sp.n_pairs; ++pr) {
+          const auto& tlist = sp.terms[set][pr];
+          if ((int)tlist.size() > kMaxTerms) return fail(c, BBLOCK_ERR_UNSUPPORTED, "too many terms");
+          int offs[kMaxTerms];
+          double2 w[kMaxTerms];
+          for (size_t t = 0; t < tlist.size(); ++t) { offs[t] = tlist[t].first * n_ev; w[t] = tlist[t].second; }
+          q3[set][pr] = add_field(j.phi[2], j.nd[2], (int)tlist.size(), offs, w);
+        }
+      base = c->d_ws + align_up((size_t)(base - c->d_ws), 256);
+      double2* partial = reinterpret_cast<double2*>(base);
+      base += align_up((size_t)n_slab * n_mom * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(double2), 256);
+      ws = base;
+      const int m_tiles = (j.nd[0] * j.nd[1] + 16 * tl.rm - 1) / (16 * tl.rm);
+      const int n_tiles = (j.nd[2] + 16 * tl.rn - 1) / (16 * tl.rn);
+      for (int set = 0; set < sp.n_coef_sets; ++set) {
+        ContractJob& cj = cjobs[set][k];
+        for (int i = 0; i < 4; ++i) { cj.q1[i] = q1[i]; cj.q2[i] = q2[i]; }
+        for (int pr = 0; pr < sp.n_pairs; ++pr) cj.q3[pr] = q3[set][pr];
+        cj.partial = partial;
+        cj.B = j.B;
+        cj.nd1 = j.nd[0]; cj.nd2 = j.nd[1]; cj.nd3 = j.nd[2];
+        cj.m_tiles = m_tiles;
+        cj.n_tiles = n_tiles;
+        cj.unit_begin = unit;
+      }
+      unit += (long long)m_tiles * n_tiles * n_slab;
+    }
+    // one contiguous table upload: fields, then one job table per coefficient set
+    const size_t fbytes = align_up(fields.size() * sizeof(ProjField), 256);
+    const size_t jbytes = align_up((size_t)nj * sizeof(ContractJob), 256);
+    std::vector<char> tab(fbytes + jbytes * sp.n_coef_sets);
+    memcpy(tab.data(), fields.data(), fields.size() * sizeof(ProjField));
+    for (int set = 0; set < sp.n_coef_sets; ++set)
+      memcpy(tab.data() + fbytes + jbytes * set, cjobs[set].data(), (size_t)nj * sizeof(ContractJob));
+    rc = upload_tables(c, tab.data(), tab.size(), s);
+    if (rc) return rc;
+    const ProjField* d_fields = reinterpret_cast<const ProjField*>(c->d_tab);
+
+    CK(c, timed_launch(c, K_PROJECT, s, [&] {
+      return launch_project_fp64(d_fields, (int)fields.size(), rows, n_ev, max_ndf, s);
+    }));
+
+    ContractParams prm{};
+    prm.n_jobs = nj;
+    prm.total_units = unit;
+    prm.X = X;
+    prm.n_slab = n_slab;
+    prm.sites_per_slab = sites_per_slab;
+    prm.n_pairs = sp.n_pairs;
+    for (int pr = 0; pr < sp.n_pairs; ++pr) { prm.a_slot[pr] = sp.a_slot[pr]; prm.b_slot[pr] = sp.b_slot[pr]; }
+    prm.phase = c->d_phase;
+    prm.P_total = n_mom;
+    prm.status = c->d_status;
+    const int grid = (int)std::min<long long>(unit, ctas);
+    if (per_mom) {
+      for (int p = 0; p < n_mom; ++p) {
+        prm.jobs = reinterpret_cast<const ContractJob*>(c->d_tab + fbytes + jbytes * p);
+        prm.p0 = p;
+        CK(c, timed_launch(c, K_CONTRACT, s, [&] { return launch_contract_fp64(prm, 1, tl.rn, grid, s); }));
+      }
+    } else {
+      prm.jobs = reinterpret_cast<const ContractJob*>(c->d_tab + fbytes);
+      for (int p0 = 0; p0 < n_mom; p0 += kMaxPGroup) {
+        const int Pg = std::min(kMaxPGroup, n_mom - p0);
+        prm.p0 = p0;
+        CK(c, timed_launch(c, K_CONTRACT, s, [&] { return launch_contract_fp64(prm, Pg, tl.rn, grid, s); }));
+      }
+    }
+    CK(c, timed_launch(c, K_REDUCE, s, [&] {
+      return launch_reduce_slabs(reinterpret_cast<const ContractJob*>(c->d_tab + fbytes), nj,
+                                 n_slab, n_mom, max_elems, s);
+    }));
+    job_idx = end;
+  }
+  return BBLOCK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bblock_create(bblock_ctx** out, const bblock_config* cfg) {
+  if (!out) return BBLOCK_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg) return BBLOCK_ERR_INVALID_ARG;
+  if (cfg->L < 1 || cfg->L > 128) return BBLOCK_ERR_INVALID_ARG;
+  const long long X = (long long)cfg->L * cfg->L * cfg->L;
+  if (cfg->n_ev < 1 || cfg->n_ev > 3 * X) return BBLOCK_ERR_INVALID_ARG;
+  if (cfg->max_ndil < 1 || cfg->max_ndil > 256) return BBLOCK_ERR_INVALID_ARG;
+  if (cfg->precision < BBLOCK_FP64 || cfg->precision > BBLOCK_BF16_SPLIT) return BBLOCK_ERR_INVALID_ARG;
+  if (cfg->precision == BBLOCK_BF16_SPLIT && cfg->bf16_products != 3 && cfg->bf16_products != 6 &&
+      cfg->bf16_products != 9)
+    return BBLOCK_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return BBLOCK_ERR_CUDA;
+  }
+  if (cfg->device < 0 || cfg->device >= ndev) return BBLOCK_ERR_INVALID_ARG;
+  bblock_ctx* c = new bblock_ctx();
+  c->cfg = *cfg;
+  c->X = (int)X;
+  c->rows = (int)(3 * X);
+  if (cudaSetDevice(cfg->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess ||
+      cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->tab_free, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    bblock_destroy(c);
+    return BBLOCK_ERR_CUDA;
+  }
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  c->ws_budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
+  *out = c;
+  return BBLOCK_OK;
+}
+
+void bblock_destroy(bblock_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->cfg.device);
+  cudaDeviceSynchronize();
+  cudaFree(c->d_status);
+  cudaFree(c->d_phase);
+  cudaFree(c->d_mom);
+  cudaFree(c->d_ws);
+  cudaFree(c->d_tab);
+  cudaFree(c->d_io);
+  if (c->h_tab) cudaFreeHost(c->h_tab);
+  if (c->tab_free) cudaEventDestroy(c->tab_free);
+  for (auto& t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete c;
+}
+
+const char* bblock_last_error(const bblock_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int bblock_status(bblock_ctx* c) {
+  if (!c) return BBLOCK_ERR_INVALID_ARG;
+  cudaError_t e = cudaSetDevice(c->cfg.device);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bblock_status");
+  int st = 0;
+  e = cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bblock_status readback");
+  if (st) return fail(c, BBLOCK_ERR_DEVICE_FLAG, "device status word 0x%x", st);
+  return BBLOCK_OK;
+}
+
+int bblock_compute(bblock_ctx* c, int n_t, const void* V, const void* phi1, const void* phi2,
+                   const void* phi3, int nd1, int nd2, int nd3, const int32_t* momenta, int n_mom,
+                   const int32_t* spin_idx, const double* spin_coeffs, int n_spin, int coeff_per_mom,
+                   void* B_out, void* stream) {
+  if (!c) return BBLOCK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (n_t < 0) return fail(c, BBLOCK_ERR_INVALID_ARG, "n_t = %d < 0", n_t);
+  int rc = validate_common(c, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom);
+  if (rc) return rc;
+  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; return BBLOCK_OK; }
+  const size_t vstride = (size_t)c->cfg.n_ev * c->rows;
+  const size_t pst[3] = {(size_t)4 * c->cfg.n_ev * nd1, (size_t)4 * c->cfg.n_ev * nd2,
+                         (size_t)4 * c->cfg.n_ev * nd3};
+  const size_t bstride = (size_t)n_mom * nd1 * nd2 * nd3;
+  if (!V || !phi1 || !phi2 || !phi3 || !B_out)
+    return fail(c, BBLOCK_ERR_INVALID_ARG, "a data pointer is NULL");
+  std::vector<JobIn> jobs(n_t);
+  for (int t = 0; t < n_t; ++t) {
+    JobIn& j = jobs[t];
+    j.V = static_cast<const double2*>(V) + t * vstride;
+    j.phi[0] = static_cast<const double2*>(phi1) + t * pst[0];
+    j.phi[1] = static_cast<const double2*>(phi2) + t * pst[1];
+    j.phi[2] = static_cast<const double2*>(phi3) + t * pst[2];
+    j.nd[0] = nd1; j.nd[1] = nd2; j.nd[2] = nd3;
+    j.B = static_cast<double2*>(B_out) + t * bstride;
+    if (t == 0) {
+      rc = validate_job(c, j, 0, true);
+      if (rc) return rc;
+    }
+  }
+  return run_jobs(c, jobs, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom,
+                  static_cast<cudaStream_t>(stream));
+}
+
+int bblock_compute_batch(bblock_ctx* c, const bblock_job* jobs_in, int n_jobs,
+                         const int32_t* momenta, int n_mom, const int32_t* spin_idx,
+                         const double* spin_coeffs, int n_spin, int coeff_per_mom, void* stream) {
+  if (!c) return BBLOCK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (n_jobs < 0 || (n_jobs > 0 && !jobs_in)) return fail(c, BBLOCK_ERR_INVALID_ARG, "bad job list");
+  int rc = validate_common(c, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom);
+  if (rc) return rc;
+  std::vector<JobIn> jobs(n_jobs);
+  for (int k = 0; k < n_jobs; ++k) {
+    JobIn& j = jobs[k];
+    j.V = static_cast<const double2*>(jobs_in[k].V);
+    j.phi[0] = static_cast<const double2*>(jobs_in[k].phi1);
+    j.phi[1] = static_cast<const double2*>(jobs_in[k].phi2);
+    j.phi[2] = static_cast<const double2*>(jobs_in[k].phi3);
+    j.nd[0] = jobs_in[k].nd1; j.nd[1] = jobs_in[k].nd2; j.nd[2] = jobs_in[k].nd3;
+    j.B = static_cast<double2*>(jobs_in[k].B_out);
+    rc = validate_job(c, j, k, true);
+    if (rc) return rc;
+  }
+  // dilution sizes may differ per job: larger jobs first so the persistent grid ends evenly
+  std::stable_sort(jobs.begin(), jobs.end(), [](const JobIn& a, const JobIn& b) {
+    return (long long)a.nd[0] * a.nd[1] * a.nd[2] > (long long)b.nd[0] * b.nd[1] * b.nd[2];
+  });
+  return run_jobs(c, jobs, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom,
+                  static_cast<cudaStream_t>(stream));
+}
+
+int bblock_compute_host(bblock_ctx* c, int n_t, const void* V, const void* phi1, const void* phi2,
+                        const void* phi3, int nd1, int nd2, int nd3, const int32_t* momenta,
+                        int n_mom, const int32_t* spin_idx, const double* spin_coeffs, int n_spin,
+                        int coeff_per_mom, void* B_out, void* stream) {
+  if (!c) return BBLOCK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (n_t < 0) return fail(c, BBLOCK_ERR_INVALID_ARG, "n_t = %d < 0", n_t);
+  int rc = validate_common(c, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom);
+  if (rc) return rc;
+  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; return BBLOCK_OK; }
+  if (!V || !phi1 || !phi2 || !phi3 || !B_out) return fail(c, BBLOCK_ERR_INVALID_ARG, "a data pointer is NULL");
+  const int nds[3] = {nd1, nd2, nd3};
+  for (int i = 0; i < 3; ++i)
+    if (nds[i] < 1 || nds[i] > c->cfg.max_ndil)
+      return fail(c, BBLOCK_ERR_INVALID_ARG, "nd%d = %d outside 1..max_ndil", i + 1, nds[i]);
+  const size_t vb = sizeof(double2) * (size_t)n_t * c->cfg.n_ev * c->rows;
+  size_t pb[3];
+  for (int i = 0; i < 3; ++i) pb[i] = sizeof(double2) * (size_t)n_t * 4 * c->cfg.n_ev * nds[i];
+  const size_t bb_ = sizeof(double2) * (size_t)n_t * n_mom * nd1 * nd2 * nd3;
+  const size_t off[5] = {0, align_up(vb, 256), align_up(vb, 256) + align_up(pb[0], 256),
+                         align_up(vb, 256) + align_up(pb[0], 256) + align_up(pb[1], 256),
+                         align_up(vb, 256) + align_up(pb[0], 256) + align_up(pb[1], 256) + align_up(pb[2], 256)};
+  CK(c, cudaSetDevice(c->cfg.device));
+  rc = grow_device(c, &c->d_io, &c->io_cap, off[4] + align_up(bb_, 256));
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(c, cudaMemcpyAsync(c->d_io + off[0], V, vb, cudaMemcpyHostToDevice, s));
+  CK(c, cudaMemcpyAsync(c->d_io + off[1], phi1, pb[0], cudaMemcpyHostToDevice, s));
+  CK(c, cudaMemcpyAsync(c->d_io + off[2], phi2, pb[1], cudaMemcpyHostToDevice, s));
+  CK(c, cudaMemcpyAsync(c->d_io + off[3], phi3, pb[2], cudaMemcpyHostToDevice, s));
+  rc = bblock_compute(c, n_t, c->d_io + off[0], c->d_io + off[1], c->d_io + off[2], c->d_io + off[3],
+                      nd1, nd2, nd3, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom,
+                      c->d_io + off[4], stream);
+  if (rc) return rc;
+  CK(c, cudaMemcpyAsync(B_out, c->d_io + off[4], bb_, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  return BBLOCK_OK;
+}
+
+size_t bblock_workspace_bytes(const bblock_ctx* c) {
+  if (!c) return 0;
+  return c->ws_cap + c->phase_cap + c->mom_cap + c->tab_cap + c->io_cap + sizeof(int);
+}
+
+int bblock_last_launch_count(const bblock_ctx* c) { return c ? c->last_launches : 0; }
+
+int bblock_profile_enable(bblock_ctx* c, int enable) {
+  if (!c) return BBLOCK_ERR_INVALID_ARG;
+  c->prof = enable != 0;
+  return BBLOCK_OK;
+}
+
+int bblock_profile_read(bblock_ctx* c, bblock_kernel_stat* out, int max_entries, int* n_entries) {
+  if (!c || (!out && max_entries > 0) || !n_entries) return BBLOCK_ERR_INVALID_ARG;
+  double ms[K_COUNT] = {};
+  int cnt[K_COUNT] = {};
+  int rc = BBLOCK_OK;
+  for (auto& t : c->timed) {
+    float m = 0.f;
+    cudaError_t e = cudaEventSynchronize(t.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m, t.a, t.b);
+    if (e != cudaSuccess && rc == BBLOCK_OK) rc = cuda_fail(c, e, "bblock_profile_read");
+    ms[t.kind] += m;
+    cnt[t.kind] += 1;
+    c->ev_pool.push_back(t.a);
+    c->ev_pool.push_back(t.b);
+  }
+  c->timed.clear();
+  int n = 0;
+  for (int k = 0; k < K_COUNT; ++k) {
+    if (!cnt[k]) continue;
+    if (n < max_entries) {
+      snprintf(out[n].name, sizeof(out[n].name), "%s", kKernelNames[k]);
+      out[n].launches = cnt[k];
+      out[n].total_ms = ms[k];
+    }
+    ++n;
+  }
+  *n_entries = n < max_entries ? n : max_entries;
+  return rc;
+}
+
+}  // extern "C"

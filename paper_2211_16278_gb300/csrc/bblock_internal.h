@@ -1,0 +1,85 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace bb {
+
+constexpr int kMaxTerms = 4;    // distinct gamma spins folded into one line-3 field
+constexpr int kMaxPairs = 16;   // distinct (alpha, beta) spin pairs
+constexpr int kMaxPGroup = 8;   // momenta handled by one contraction launch
+constexpr int kThreads = 256;   // threads per CTA of the FP64 kernels
+
+// Device-side status bits (OR-ed into the context's status word).
+constexpr int kStatusBadJob = 1;
+
+// One reconstructed field of Eq. (2):
+//   q[r][d] = sum_l V[l][r] * Phi[l][d],   Phi[l][d] = sum_t w[t] * phi[row_off[t] + l][d],
+// r = 3x + a running over the 3X (site, colour) rows. Lines 1 and 2 use one term
+// (row_off = alpha * n_ev, w = 1); line 3 folds the spin coefficients of every
+// triple that shares an (alpha, beta) pair into one field (Eq. 1 is linear in q3).
+struct ProjField {
+  const double2* V;     // [n_ev][3X]
+  const double2* phi;   // [4 n_ev][nd]
+  double2* q;           // [3X][nd]
+  int nd;
+  int n_terms;
+  int row_off[kMaxTerms];
+  double2 w[kMaxTerms];
+};
+
+// Same field, FP32 output for the tensor-core forms.
+struct ProjFieldF {
+  const double2* V;
+  const double2* phi;
+  float2* q;
+  int nd;
+  int n_terms;
+  int row_off[kMaxTerms];
+  double2 w[kMaxTerms];
+};
+
+// One job = one time slice of one noise triple.
+struct ContractJob {
+  const double2* q1[4];          // line-1 fields, one per distinct alpha (slot order)
+  const double2* q2[4];          // line-2 fields, one per distinct beta
+  const double2* q3[kMaxPairs];  // folded line-3 field per (alpha, beta) pair
+  double2* partial;              // [n_slab][P_total][nd1*nd2][nd3]
+  double2* B;                    // [P_total][nd1][nd2][nd3]
+  int nd1, nd2, nd3;
+  int m_tiles, n_tiles;
+  long long unit_begin;          // first global work-unit index of this job
+};
+
+struct ContractParams {
+  const ContractJob* jobs;
+  int n_jobs;
+  long long total_units;
+  int X;                         // sites per time slice
+  int n_slab;
+  int sites_per_slab;
+  int n_pairs;
+  int a_slot[kMaxPairs];         // pair -> line-1 slot
+  int b_slot[kMaxPairs];         // pair -> line-2 slot
+  const double2* phase;          // [P_total][X]
+  int p0;                        // first momentum of this launch
+  int P_total;
+  int* status;
+};
+
+// Tiles of the FP64 contraction for a momentum count (per launch).
+struct Fp64Tile { int rm, rn; };
+inline Fp64Tile fp64_tile_for(int P) { return P <= 4 ? Fp64Tile{2, 2} : Fp64Tile{2, 1}; }
+inline int fp64_sites_per_chunk(int n_pairs) { return n_pairs >= 16 ? 1 : 16 / n_pairs; }
+size_t fp64_contract_smem_bytes(int P, int rn, int n_pairs);
+
+cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, cudaStream_t s);
+cudaError_t launch_project_fp64(const ProjField* d_fields, int n_fields, int rows, int n_ev,
+                                int max_nd, cudaStream_t s);
+cudaError_t launch_contract_fp64(const ContractParams& p, int P, int rn, int grid, cudaStream_t s);
+int fp64_contract_ctas_per_sm(int P, int rn, int n_pairs);
+cudaError_t launch_reduce_slabs(const ContractJob* d_jobs, int n_jobs, int n_slab, int P_total,
+                                long long max_elems, cudaStream_t s);
+
+}  // namespace bb
