@@ -52,6 +52,7 @@ extern "C" {
 #define BBLOCK_ERR_CUDA (-4)         /* a CUDA runtime call failed */
 #define BBLOCK_ERR_TIMEOUT (-5)      /* a bounded device wait gave up */
 #define BBLOCK_ERR_DEVICE_FLAG (-6)  /* a kernel flagged an inconsistent job table */
+#define BBLOCK_ERR_TOO_LARGE (-7)    /* request exceeds the fixed scratch of bblock_contract_noalloc */
 
 /* Arithmetic of the projection and the contraction. */
 typedef enum {
@@ -150,6 +151,40 @@ int bblock_profile_enable(bblock_ctx* ctx, int enable);
  * out (one entry per kernel name that launched), set *n_entries, and reset. */
 int bblock_profile_read(bblock_ctx* ctx, bblock_kernel_stat* out, int max_entries,
                         int* n_entries);
+
+/* Size of the fixed device scratch used by bblock_contract_noalloc (32 MiB). */
+#define BBLOCK_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* Allocation-free contraction. The paper has no counterpart: this entry point exists
+ * for callers that must not allocate device memory, such as applications whose memory
+ * manager has reserved the device's memory up front (a pooled allocator of a larger
+ * code, or solver fields that fill HBM), or hot loops that forbid cudaMalloc/cudaFree
+ * because those calls synchronise the whole device.
+ *
+ * It computes the same blocks as bblock_compute for one time slice, but from fields that
+ * are already reconstructed, and needs no context:
+ *   q1, q2, q3  complex128 [4][L^3][3][nd_i], device memory of the CURRENT device,
+ *               q_i[alpha][x][a][d] as in Eq. (2) (spins a caller does not use may hold
+ *               anything; they are not read);
+ *   B_out       complex128 [n_mom][nd1][nd2][nd3], device memory of the current device;
+ *   momenta, spin_idx, spin_coeffs: host arrays as for bblock_compute, with one
+ *               coefficient per spin triple (no per-momentum coefficients);
+ *   stream      the cudaStream_t the two kernels are enqueued on (not awaited);
+ *   err         optional host buffer of err_len bytes for a one-line message.
+ * Limits: n_mom <= 8 and n_mom*nd1*nd2*nd3*16 <= BBLOCK_NOALLOC_SCRATCH_BYTES; larger
+ * requests return BBLOCK_ERR_TOO_LARGE without launching anything.
+ * The per-slab partial sums live in one file-scope device array of
+ * BBLOCK_NOALLOC_SCRATCH_BYTES that every device loading the library holds until the
+ * process exits. It calls no cudaMalloc, cudaFree or other allocating routine. The
+ * first call on a device looks up that array's device address (cudaGetSymbolAddress,
+ * with the device current); make that first call before any stream capture. All calls
+ * share the one array and every call overwrites the part it reads, so calls that overlap
+ * on the GPU (different streams or host threads without ordering between them) race and
+ * must be serialised by the caller. */
+int bblock_contract_noalloc(int L, const void* q1, const void* q2, const void* q3, int nd1,
+                            int nd2, int nd3, const int32_t* momenta, int n_mom,
+                            const int32_t* spin_idx, const double* spin_coeffs, int n_spin,
+                            void* B_out, void* stream, char* err, size_t err_len);
 
 #ifdef __cplusplus
 }

@@ -25,6 +25,7 @@ ERRORS = {
     -4: "BBLOCK_ERR_CUDA",
     -5: "BBLOCK_ERR_TIMEOUT",
     -6: "BBLOCK_ERR_DEVICE_FLAG",
+    -7: "BBLOCK_ERR_TOO_LARGE",
 }
 PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16": 2}
 
@@ -33,6 +34,7 @@ EXPORTED = (
     "bblock_create", "bblock_destroy", "bblock_last_error", "bblock_status", "bblock_compute",
     "bblock_compute_host", "bblock_compute_batch", "bblock_workspace_bytes",
     "bblock_last_launch_count", "bblock_profile_enable", "bblock_profile_read",
+    "bblock_contract_noalloc",
 )
 
 
@@ -95,6 +97,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bblock_profile_read.argtypes = [P, ctypes.POINTER(bblock_kernel_stat), I,
                                         ctypes.POINTER(I)]
     lib.bblock_profile_read.restype = I
+    lib.bblock_contract_noalloc.argtypes = [I, P, P, P, I, I, I, P, I, P, P, I, P, P,
+                                            ctypes.c_char_p, ctypes.c_size_t]
+    lib.bblock_contract_noalloc.restype = I
     _lib = lib
     return lib
 
@@ -268,3 +273,29 @@ def bblock_compute_batch(ctx: Context, jobs: Sequence[tuple], momenta, spin_idx,
                                      spins.ctypes.data, coeffs.ctypes.data, spins.shape[0],
                                      per_mom, _stream_handle(stream))
     _check(ctx, rc)
+
+
+def bblock_contract_noalloc(L: int, q1, q2, q3, momenta, spin_idx, spin_coeffs, B_out,
+                            stream=None):
+    """Allocation-free contraction from reconstructed fields q_i[alpha][x][a][d]
+    (device complex128 [4][L^3][3][nd_i]) into B_out [n_mom][nd1][nd2][nd3]; see
+    include/bblock.h. For callers that must not allocate device memory."""
+    X = L ** 3
+    nds = []
+    for i, q in enumerate((q1, q2, q3)):
+        if q.ndim != 4 or tuple(q.shape[:3]) != (4, X, 3):
+            raise ValueError(f"q{i + 1} must have shape (4, L^3, 3, nd)")
+        nds.append(int(q.shape[3]))
+    mom, spins, coeffs, per_mom = _spin_arrays(momenta, spin_idx, spin_coeffs)
+    if per_mom:
+        raise ValueError("bblock_contract_noalloc takes one coefficient per spin triple")
+    if tuple(B_out.shape) != (mom.shape[0], *nds):
+        raise ValueError("B_out must have shape (n_mom, nd1, nd2, nd3)")
+    err = ctypes.create_string_buffer(256)
+    rc = load().bblock_contract_noalloc(
+        L, _dev_ptr(q1, "q1"), _dev_ptr(q2, "q2"), _dev_ptr(q3, "q3"), nds[0], nds[1], nds[2],
+        mom.ctypes.data, mom.shape[0], spins.ctypes.data, coeffs.ctypes.data, spins.shape[0],
+        _dev_ptr(B_out, "B_out"), _stream_handle(stream), err, len(err))
+    if rc != BBLOCK_OK:
+        raise BblockError(rc, err.value.decode())
+    return B_out
