@@ -39,6 +39,20 @@ UNIT = "blocks/s"
 # Peak of the FP64 pipe: the nominal 1.25 TFLOP/s of GB300 is 4 FP64 flop/clk/SM
 # (2 DFMA) x 152 SMs x the 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 4 * 152 * 2.070e9 / 1e12
+
+
+def _measured_peaks():
+    """Dense BF16 tensor peak measured on the GB300s (cuBLAS burst), if present."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# BF16 from the measured burst figure (fallback 1.9 PFLOP/s); TF32 = BF16 x the nominal
+# dense ratio 1.1 / 2.25.
+BF16_PEAK_TFLOPS = float(_measured_peaks().get("bf16_tflops", 1900.0))
+TF32_PEAK_TFLOPS = BF16_PEAK_TFLOPS * 1.1 / 2.25
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -55,6 +69,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU seconds of one oracle sample")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the tensor-core forms (time the FP64 form only)")
     ap.add_argument("--n-t", type=int, default=None,
                     help="time slices per step (default: the workload's); for profiling runs")
     return ap.parse_args()
@@ -252,44 +268,54 @@ def run_ours(args):
     n_alpha, n_beta, pairs = spin_structure(inp.spins)
     V = torch.from_numpy(inp.V).to(dev)
     phis = [torch.from_numpy(inp.phi[0][i]).to(dev) for i in range(3)]
-    B = torch.empty((w.n_t, P, *nd), dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = bb.bblock_create(w.L, w.n_ev, max(nd), "fp64", device=local)
+    blocks_per_step = w.n_t * P
 
-    def step():
-        bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B,
-                          stream=stream)
+    def measure(precision, products, sampler=None):
+        """W untimed + K timed steps of one form; CUDA events on the launching stream."""
+        c = bb.bblock_create(w.L, w.n_ev, max(nd), precision, bf16_products=products,
+                             device=local)
+        out = torch.empty((w.n_t, P, *nd), dtype=torch.complex128, device=dev)
 
-    for _ in range(args.warmup):
-        step()
-    bb.bblock_status(ctx)
-    torch.cuda.synchronize(dev)
-    barrier()
+        def step():
+            bb.bblock_compute(c, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=out,
+                              stream=stream)
 
-    bb.bblock_profile_enable(ctx, True)
-    bb.bblock_profile_read(ctx)  # reset
-    launches = 0
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step()
+        bb.bblock_status(c)
+        torch.cuda.synchronize(dev)
+        barrier()
+        bb.bblock_profile_enable(c, True)
+        bb.bblock_profile_read(c)  # reset
+        n_launch = 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if sampler is not None:
+            sampler.__enter__()
         torch.cuda.synchronize(dev)
         barrier()
         e0.record(stream)
         for _ in range(args.steps):
             step()
-            launches += bb.bblock_last_launch_count(ctx)
+            n_launch += bb.bblock_last_launch_count(c)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-    bb.bblock_status(ctx)
-    ms = e0.elapsed_time(e1)
-    prof = bb.bblock_profile_read(ctx)
-    bb.bblock_profile_enable(ctx, False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    blocks_per_step = w.n_t * P
+        if sampler is not None:
+            sampler.__exit__(None, None, None)
+        bb.bblock_status(c)
+        t_ms = e0.elapsed_time(e1)
+        prof = bb.bblock_profile_read(c)
+        bb.bblock_profile_enable(c, False)
+        if world > 1:
+            t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_ms = float(t.item())
+        return c, out, t_ms, prof, n_launch
+
+    clk = ClockSampler(local)
+    ctx, B, ms, prof, launches = measure("fp64", 6, clk)
     value = world * blocks_per_step * args.steps / (ms / 1e3)
 
     # roofline of the dominant kernel (the contraction): algorithmic flops / event time
@@ -308,6 +334,34 @@ def run_ours(args):
     }
     kernels = {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / ms if ms else None}
                for k, v in prof.items()}
+
+    # the tensor-core forms on the same inputs; error against the FP64 form's blocks
+    forms = {}
+    if not args.no_forms:
+        B64 = B.cpu().numpy()
+        nrm = np.linalg.norm(B64)
+        # useful complex GEMM work of the folded contraction: 8 M N K per job, K = 3 pairs X
+        gemm_flops = w.n_t * 8.0 * nd[0] * nd[1] * (P * nd[2]) * (3 * pairs * w.X)
+        for name, prec, prods, nprod, peak in (
+                ("bf16x6", "bf16", 6, 6, BF16_PEAK_TFLOPS), ("bf16x9", "bf16", 9, 9, BF16_PEAK_TFLOPS),
+                ("tf32x3", "tf32x3", 6, 3, TF32_PEAK_TFLOPS), ("bf16x3", "bf16", 3, 3, BF16_PEAK_TFLOPS)):
+            c2, out, t_ms, pr, nl = measure(prec, prods)
+            err = float(np.linalg.norm(out.cpu().numpy() - B64) / nrm)
+            nc, msc = pr.get("contract", (0, 0.0))
+            execd = gemm_flops * nprod / (msc / nc / 1e3) / 1e12 if nc else None
+            forms[name] = {
+                "blocks_per_s": world * blocks_per_step * args.steps / (t_ms / 1e3),
+                "ms_per_step": t_ms / args.steps, "gpu_launches": nl,
+                "rel_frobenius_err_vs_fp64_form": err,
+                "speedup_vs_fp64_form": ms / t_ms,
+                "contract_ms_per_launch": msc / nc if nc else None,
+                "tensor_roofline": {"bound": "tensor", "achieved": execd, "peak": peak,
+                                    "unit": "TFLOP/s", "frac": execd / peak if execd else None,
+                                    "flops": "executed split-product MMA flops"},
+                "kernels": {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / t_ms}
+                            for k, v in pr.items()},
+            }
+            bb.bblock_destroy(c2)
 
     # end to end through the host-buffer entry point: H2D inputs + compute + D2H blocks
     e2e = None
@@ -358,6 +412,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     bb.bblock_destroy(ctx)

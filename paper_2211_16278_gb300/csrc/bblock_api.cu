@@ -277,6 +277,176 @@ int validate_job(bblock_ctx* c, const JobIn& j, int idx, bool device) {
   return BBLOCK_OK;
 }
 
+int tc_form_of(const bblock_config& cfg) {
+  if (cfg.precision == BBLOCK_TF32X3) return TC_TF32_3;
+  return cfg.bf16_products == 3 ? TC_BF16_3 : cfg.bf16_products == 9 ? TC_BF16_9 : TC_BF16_6;
+}
+
+// Complex columns per tensor-core tile: the N tile that wastes the fewest padded columns,
+// counting a fixed per-tile cost of 16 columns for building the shared diquark tile.
+int choose_nc(const std::vector<JobIn>& jobs, size_t b, size_t e, int P) {
+  int best = 48;
+  long long best_cost = -1;
+  for (int nc = 48; nc >= 16; nc -= 16) {
+    long long cost = 0;
+    for (size_t k = b; k < e; ++k) {
+      const long long N = (long long)P * jobs[k].nd[2];
+      const long long mt = ((long long)jobs[k].nd[0] * jobs[k].nd[1] + 127) / 128;
+      cost += mt * ((N + nc - 1) / nc) * (nc + 16);
+    }
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = nc; }
+  }
+  return best;
+}
+
+// Tensor-core forms: FP32 projection, tcgen05 contraction, FP64 slab reduction.
+int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& sp, int n_mom,
+                int per_mom, cudaStream_t s) {
+  const int X = c->X, rows = c->rows, n_ev = c->cfg.n_ev;
+  const int form = tc_form_of(c->cfg);
+  const int G = tc_groups_per_stage(form);
+  const int chunk_stages = 2;                 // 12 leading accumulations between drains
+  const int n3_fields = sp.n_pairs * sp.n_coef_sets;
+  const int P_launch = per_mom ? 1 : n_mom;
+  const int grid_cap = c->num_sms;            // one CTA per SM (all of TMEM, ~200 KB smem)
+  // at most 256 drains into the FP32 running sum per work unit
+  const long long max_groups_per_unit = 256LL * chunk_stages * G;
+  const int min_slabs = (int)std::min<long long>(
+      X, ((long long)X * sp.n_pairs + max_groups_per_unit - 1) / max_groups_per_unit);
+  const int max_slabs = std::max(64, min_slabs);
+  auto job_bytes = [&](const JobIn& j, int n_slab) {
+    size_t f = (size_t)rows * (sp.n1 * j.nd[0] + sp.n2 * j.nd[1] + n3_fields * j.nd[2]) * sizeof(float2);
+    size_t p = (size_t)n_slab * P_launch * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(float2);
+    return align_up(f, 256) + align_up(p, 256);
+  };
+  size_t job_idx = 0;
+  int rc;
+  while (job_idx < jobs.size()) {
+    size_t end = job_idx, need = 0;
+    while (end < jobs.size()) {
+      size_t b = job_bytes(jobs[end], max_slabs);
+      if (end > job_idx && need + b > c->ws_budget) break;
+      need += b;
+      ++end;
+    }
+    const int nj = (int)(end - job_idx);
+    const int NC = choose_nc(jobs, job_idx, end, P_launch);
+    long long tiles = 0, max_elems = 0;
+    int max_ndf = 0;
+    for (size_t k = job_idx; k < end; ++k) {
+      const JobIn& j = jobs[k];
+      tiles += (long long)((j.nd[0] * j.nd[1] + 127) / 128) * ((P_launch * j.nd[2] + NC - 1) / NC);
+      for (int i = 0; i < 3; ++i) max_ndf = std::max(max_ndf, j.nd[i]);
+      max_elems = std::max(max_elems, (long long)P_launch * j.nd[0] * j.nd[1] * j.nd[2]);
+    }
+    int n_slab = std::max(min_slabs, choose_slabs(tiles, grid_cap, X, 1, max_slabs));
+    int sites_per_slab = (X + n_slab - 1) / n_slab;
+    n_slab = (X + sites_per_slab - 1) / sites_per_slab;
+    size_t ws_need = 0;
+    for (size_t k = job_idx; k < end; ++k) ws_need += job_bytes(jobs[k], n_slab);
+    rc = grow_device(c, &c->d_ws, &c->ws_cap, ws_need);
+    if (rc) return rc;
+
+    std::vector<ProjFieldF> fields;
+    std::vector<std::vector<TcJob>> tjobs(sp.n_coef_sets, std::vector<TcJob>(nj));
+    char* ws = c->d_ws;
+    long long unit = 0;
+    for (int k = 0; k < nj; ++k) {
+      const JobIn& j = jobs[job_idx + k];
+      char* base = ws;
+      auto add_field = [&](const double2* phi, int nd, int n_terms, const int* offs,
+                           const double2* w) -> float2* {
+        ProjFieldF f{};
+        f.V = j.V;
+        f.phi = phi;
+        f.q = reinterpret_cast<float2*>(base);
+        f.nd = nd;
+        f.n_terms = n_terms;
+        for (int t = 0; t < n_terms; ++t) { f.row_off[t] = offs[t]; f.w[t] = w[t]; }
+        base += (size_t)rows * nd * sizeof(float2);
+        fields.push_back(f);
+        return f.q;
+      };
+      const double2 one = make_double2(1.0, 0.0);
+      const float2* q1[4] = {};
+      const float2* q2[4] = {};
+      for (int sl = 0; sl < sp.n1; ++sl) {
+        int off = sp.alpha_of1[sl] * n_ev;
+        q1[sl] = add_field(j.phi[0], j.nd[0], 1, &off, &one);
+      }
+      for (int sl = 0; sl < sp.n2; ++sl) {
+        int off = sp.beta_of2[sl] * n_ev;
+        q2[sl] = add_field(j.phi[1], j.nd[1], 1, &off, &one);
+      }
+      std::vector<std::vector<const float2*>> q3(sp.n_coef_sets, std::vector<const float2*>(sp.n_pairs));
+      for (int set = 0; set < sp.n_coef_sets; ++set)
+        for (int pr = 0; pr < sp.n_pairs; ++pr) {
+          const auto& tlist = sp.terms[set][pr];
+          if ((int)tlist.size() > kMaxTerms) return fail(c, BBLOCK_ERR_UNSUPPORTED, "too many terms");
+          int offs[kMaxTerms];
+          double2 w[kMaxTerms];
+          for (size_t t = 0; t < tlist.size(); ++t) { offs[t] = tlist[t].first * n_ev; w[t] = tlist[t].second; }
+          q3[set][pr] = add_field(j.phi[2], j.nd[2], (int)tlist.size(), offs, w);
+        }
+      base = c->d_ws + align_up((size_t)(base - c->d_ws), 256);
+      float2* partial = reinterpret_cast<float2*>(base);
+      base += align_up((size_t)n_slab * P_launch * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(float2), 256);
+      ws = base;
+      const int m_tiles = (j.nd[0] * j.nd[1] + 127) / 128;
+      const int n_tiles = (P_launch * j.nd[2] + NC - 1) / NC;
+      for (int set = 0; set < sp.n_coef_sets; ++set) {
+        TcJob& tj = tjobs[set][k];
+        for (int i = 0; i < 4; ++i) { tj.q1[i] = q1[i]; tj.q2[i] = q2[i]; }
+        for (int pr = 0; pr < sp.n_pairs; ++pr) tj.q3[pr] = q3[set][pr];
+        tj.partial = partial;
+        // per-momentum coefficient sets run one momentum per launch into their slice of B
+        tj.B = j.B + (per_mom ? (size_t)set * j.nd[0] * j.nd[1] * j.nd[2] : 0);
+        tj.nd1 = j.nd[0]; tj.nd2 = j.nd[1]; tj.nd3 = j.nd[2];
+        tj.m_tiles = m_tiles;
+        tj.n_tiles = n_tiles;
+        tj.unit_begin = unit;
+      }
+      unit += (long long)m_tiles * n_tiles * n_slab;
+    }
+    const size_t fbytes = align_up(fields.size() * sizeof(ProjFieldF), 256);
+    const size_t jbytes = align_up((size_t)nj * sizeof(TcJob), 256);
+    std::vector<char> tab(fbytes + jbytes * sp.n_coef_sets);
+    memcpy(tab.data(), fields.data(), fields.size() * sizeof(ProjFieldF));
+    for (int set = 0; set < sp.n_coef_sets; ++set)
+      memcpy(tab.data() + fbytes + jbytes * set, tjobs[set].data(), (size_t)nj * sizeof(TcJob));
+    rc = upload_tables(c, tab.data(), tab.size(), s);
+    if (rc) return rc;
+    const ProjFieldF* d_fields = reinterpret_cast<const ProjFieldF*>(c->d_tab);
+    CK(c, timed_launch(c, K_PROJECT, s, [&] {
+      return launch_project_f32(d_fields, (int)fields.size(), rows, n_ev, max_ndf, s);
+    }));
+    TcParams prm{};
+    prm.n_jobs = nj;
+    prm.total_units = unit;
+    prm.X = X;
+    prm.n_slab = n_slab;
+    prm.sites_per_slab = sites_per_slab;
+    prm.n_pairs = sp.n_pairs;
+    for (int pr = 0; pr < sp.n_pairs; ++pr) { prm.a_slot[pr] = sp.a_slot[pr]; prm.b_slot[pr] = sp.b_slot[pr]; }
+    prm.P = P_launch;
+    prm.NC = NC;
+    prm.chunk_stages = chunk_stages;
+    prm.status = c->d_status;
+    const int grid = (int)std::min<long long>(unit, grid_cap);
+    for (int set = 0; set < sp.n_coef_sets; ++set) {
+      const TcJob* d_jobs = reinterpret_cast<const TcJob*>(c->d_tab + fbytes + jbytes * set);
+      prm.jobs = d_jobs;
+      prm.phase = c->d_phase + (per_mom ? (size_t)set * X : 0);
+      CK(c, timed_launch(c, K_CONTRACT, s, [&] { return launch_contract_tc(prm, form, grid, s); }));
+      CK(c, timed_launch(c, K_REDUCE, s, [&] {
+        return launch_reduce_slabs_f32(d_jobs, nj, n_slab, P_launch, max_elems, s);
+      }));
+    }
+    job_idx = end;
+  }
+  return BBLOCK_OK;
+}
+
 // The whole launch sequence for a list of jobs sharing momenta and spin operator.
 int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momenta, int n_mom,
              const int32_t* spin_idx, const double* coeffs, int n_spin, int per_mom,
@@ -289,10 +459,9 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
   int rc = plan_spins(c, spin_idx, coeffs, n_spin, per_mom, n_mom, &sp);
   if (rc) return rc;
   if (sp.n_pairs > kMaxPairs) return fail(c, BBLOCK_ERR_UNSUPPORTED, "more than %d spin pairs", kMaxPairs);
-  if (c->cfg.precision != BBLOCK_FP64)
-    return fail(c, BBLOCK_ERR_UNSUPPORTED, "precision %d is not built yet", c->cfg.precision);
   rc = ensure_phase(c, momenta, n_mom, s);
   if (rc) return rc;
+  if (c->cfg.precision != BBLOCK_FP64) return run_jobs_tc(c, jobs, sp, n_mom, per_mom, s);
 
   const int X = c->X, rows = c->rows, n_ev = c->cfg.n_ev;
   const int n3_fields = sp.n_pairs * sp.n_coef_sets;

@@ -13,6 +13,7 @@ constexpr int kThreads = 256;   // threads per CTA of the FP64 kernels
 
 // Device-side status bits (OR-ed into the context's status word).
 constexpr int kStatusBadJob = 1;
+constexpr int kStatusTimeout = 2;   // a bounded wait of the tensor-core kernel gave up
 
 // One reconstructed field of Eq. (2):
 //   q[r][d] = sum_l V[l][r] * Phi[l][d],   Phi[l][d] = sum_t w[t] * phi[row_off[t] + l][d],
@@ -73,6 +74,46 @@ struct Fp64Tile { int rm, rn; };
 inline Fp64Tile fp64_tile_for(int P) { return P <= 4 ? Fp64Tile{2, 2} : Fp64Tile{2, 1}; }
 inline int fp64_sites_per_chunk(int n_pairs) { return n_pairs >= 16 ? 1 : 16 / n_pairs; }
 size_t fp64_contract_smem_bytes(int P, int rn, int n_pairs);
+
+// ---------------------------------------------------------------- tensor-core forms
+
+// One job of the tensor-core contraction: FP32 fields [(x,a)][d] and FP32 per-slab partials.
+struct TcJob {
+  const float2* q1[4];
+  const float2* q2[4];
+  const float2* q3[kMaxPairs];
+  float2* partial;               // [n_slab][P][nd1*nd2][nd3]
+  double2* B;                    // [P][nd1][nd2][nd3]
+  int nd1, nd2, nd3;
+  int m_tiles, n_tiles;
+  long long unit_begin;
+};
+
+struct TcParams {
+  const TcJob* jobs;
+  int n_jobs;
+  long long total_units;
+  int X;
+  int n_slab;
+  int sites_per_slab;
+  int n_pairs;
+  int a_slot[kMaxPairs];
+  int b_slot[kMaxPairs];
+  const double2* phase;          // [P][X]
+  int P;                         // momenta (columns n = p*nd3 + d3)
+  int NC;                        // complex columns per tile: 16, 32 or 48
+  int chunk_stages;              // stages accumulated in TMEM between drains
+  int* status;
+};
+
+enum TcForm { TC_BF16_3 = 0, TC_BF16_6 = 1, TC_BF16_9 = 2, TC_TF32_3 = 3 };
+
+cudaError_t launch_project_f32(const ProjFieldF* d_fields, int n_fields, int rows, int n_ev,
+                               int max_nd, cudaStream_t s);
+cudaError_t launch_contract_tc(const TcParams& p, int form, int grid, cudaStream_t s);
+int tc_groups_per_stage(int form);
+cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab, int P_total,
+                                    long long max_elems, cudaStream_t s);
 
 cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, cudaStream_t s);
 cudaError_t launch_project_fp64(const ProjField* d_fields, int n_fields, int rows, int n_ev,

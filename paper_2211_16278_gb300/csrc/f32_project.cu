@@ -1,0 +1,98 @@
+// Eq. (2) for the tensor-core forms: q = V^T Phi in FP32 with FP32 accumulation.
+//
+// The complex128 inputs are converted to FP32 while they are staged in shared memory (the
+// input-conversion step of the mixed forms); the spin coefficients of line 3 are folded
+// into the staged Phi tile as in the FP64 projection. One CTA computes a 128-row x 32-column
+// tile of one field; the grid runs the fields of a row tile back to back (blockIdx.x = field)
+// so that the V tile they share is served from L2.
+#include "bblock_internal.h"
+
+namespace bb {
+
+constexpr int FBM = 128, FBN = 32, FBK = 16;
+
+__global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __restrict__ fields,
+                                                          int rows, int n_ev) {
+  __shared__ float2 As[FBK][FBM];
+  __shared__ float2 Bs[FBK][FBN];
+  const ProjFieldF& F = fields[blockIdx.x];
+  const int nd = F.nd;
+  const int n0 = blockIdx.z * FBN;
+  if (n0 >= nd) return;
+  const int m0 = blockIdx.y * FBM;
+  const int tid = threadIdx.x, tn = tid % 8, tm = tid / 8;   // 32 x 8 threads, 4 x 4 outputs each
+  const int n_terms = F.n_terms;
+  float2 wt[kMaxTerms];
+  for (int t = 0; t < kMaxTerms; ++t)
+    wt[t] = make_float2((float)F.w[t].x, (float)F.w[t].y);
+
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+  for (int kb = 0; kb < n_ev; kb += FBK) {
+    for (int idx = tid; idx < FBK * FBM; idx += kThreads) {
+      const int r = idx % FBM, kk = idx / FBM;
+      const int l = kb + kk, row = m0 + r;
+      float2 v = make_float2(0.f, 0.f);
+      if (l < n_ev && row < rows) {
+        const double2 d = F.V[(size_t)l * rows + row];
+        v = make_float2((float)d.x, (float)d.y);
+      }
+      As[kk][r] = v;
+    }
+    for (int idx = tid; idx < FBK * FBN; idx += kThreads) {
+      const int c = idx % FBN, kk = idx / FBN;
+      const int l = kb + kk, col = n0 + c;
+      float2 b = make_float2(0.f, 0.f);
+      if (l < n_ev && col < nd) {
+        for (int t = 0; t < n_terms; ++t) {
+          const double2 d = F.phi[(size_t)(F.row_off[t] + l) * nd + col];
+          const float2 f = make_float2((float)d.x, (float)d.y);
+          b.x = fmaf(wt[t].x, f.x, fmaf(-wt[t].y, f.y, b.x));
+          b.y = fmaf(wt[t].x, f.y, fmaf(wt[t].y, f.x, b.y));
+        }
+      }
+      Bs[kk][c] = b;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < FBK; ++kk) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tm + 32 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tn + 8 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(a[i].x, b[j].y, fmaf(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = m0 + tm + 32 * i;
+    if (row >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = n0 + tn + 8 * j;
+      if (col < nd) F.q[(size_t)row * nd + col] = acc[i][j];
+    }
+  }
+}
+
+cudaError_t launch_project_f32(const ProjFieldF* d_fields, int n_fields, int rows, int n_ev,
+                               int max_nd, cudaStream_t s) {
+  if (n_fields == 0 || rows == 0) return cudaSuccess;
+  dim3 grid(n_fields, (rows + FBM - 1) / FBM, (max_nd + FBN - 1) / FBN);
+  k_project_f32<<<grid, kThreads, 0, s>>>(d_fields, rows, n_ev);
+  return cudaGetLastError();
+}
+
+}  // namespace bb

@@ -1,0 +1,560 @@
+// Tensor-core forms of the fused diquark + contraction (Eq. 1/3) on sm_103a: tcgen05 MMAs
+// with FP32 accumulators in tensor memory (TMEM), operands split into BF16 or TF32 pieces.
+//
+// The contraction is a complex GEMM per (time slice, noise triple):
+//   C[(d1,d2)][(p,d3)] += sum_k A[(d1,d2)][k] * Bop[k][(p,d3)],   k = (site, spin pair, colour)
+//   A   = diquark  (q1_alpha x q2_beta)_c(x)                       (Algorithm 1 "diq")
+//   Bop = e^{-i p.x} q3_(alpha beta)[x][c][d3]                     (singlet and phase folded)
+// Neither operand exists in HBM: producer warps build both in shared memory for every stage
+// of 16 (BF16) or 8 (TF32) (site, pair) groups, split each FP32 value into pieces
+// v = v0 + v1 (+ v2) and store them as K-major 8x16-byte core matrices; one thread issues
+// the MMAs. Complex products use separate real and imaginary planes:
+//   Cr += Ar Br - Ai Bi  (the second product with the B-negate bit),  Ci += Ar Bi + Ai Br.
+// Accuracy: the TMEM accumulator rounds towards zero, so the leading piece product (v0 w0)
+// goes to its own accumulator and is drained every `chunk_stages` stages into an FP32
+// running sum (round to nearest) kept in TMEM; the smaller correction products share a
+// second accumulator. Each work unit (job, 128 pairs, NC columns, site slab) writes its
+// running sum as an FP32 partial block; the slab partials are summed in FP64 in index order.
+//
+// Warp roles (13 warps): 0-3 epilogue (TMEM lanes 0-127: drains, partial write-out),
+// 4 MMA issue + TMEM allocation, 5-12 operand producers. Every wait is bounded; on a
+// timeout the CTA sets a status bit, stops, waits (bounded) for its MMAs and frees TMEM.
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "bblock_internal.h"
+
+namespace bb {
+namespace {
+
+constexpr int kTcM = 128;
+constexpr int kEpiWarps = 4;
+constexpr int kMmaWarp = 4;
+constexpr int kProdWarp0 = 5;
+constexpr int kProdWarps = 8;
+constexpr int kTcThreads = (kProdWarp0 + kProdWarps) * 32;
+constexpr int kProdThreads = kProdWarps * 32;
+constexpr int kTmemCols = 512;
+constexpr int kMaxNC = 48;
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s
+constexpr int kBarProd = 1, kBarEpi = 2;
+constexpr int kAPlaneBytes = kTcM * 96;          // 128 rows x 96 bytes of K per stage
+constexpr int kBPlaneBytes = kMaxNC * 96;
+constexpr int kSegsPerRow = 6;                   // 16-byte core-matrix columns per row
+
+// ------------------------------------------------------------------ PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void named_bar(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  // K-major, no swizzle: LBO = 128 B between core matrices along K, SBO = 768 B between
+  // 8-row groups; descriptor version 1.
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(768 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+  if (TF32)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16};"
+      ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+        "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])),
+        "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+        "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+        "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ operand splitting
+
+__device__ __forceinline__ float tf32_round(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+// Split 8 FP32 values into LEVELS pieces and store each piece's 8 values as one K run of
+// a core-matrix row (16 bytes of BF16, or 32 bytes = two 16-byte rows of TF32).
+template <bool TF32, int LEVELS>
+__device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const (&dst)[LEVELS]) {
+  if (!TF32) {
+    float r[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = v[i];
+#pragma unroll
+    for (int l = 0; l < LEVELS; ++l) {
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(r[2 * i], r[2 * i + 1]);
+        const float2 back = __bfloat1622float2(h);
+        r[2 * i] -= back.x;
+        r[2 * i + 1] -= back.y;
+        w[i] = *reinterpret_cast<uint32_t*>(&h);
+      }
+      *reinterpret_cast<uint4*>(dst[l]) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+    float r[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = v[i];
+#pragma unroll
+    for (int l = 0; l < LEVELS; ++l) {
+      float h[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        h[i] = tf32_round(r[i]);
+        r[i] -= h[i];
+      }
+      // a 32-byte K run spans two adjacent core matrices along K (128 bytes apart)
+      *reinterpret_cast<float4*>(dst[l]) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(dst[l] + 128) = make_float4(h[4], h[5], h[6], h[7]);
+    }
+  }
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ int tc_find_job(const TcJob* jobs, int n_jobs, long long u) {
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct Unit {
+  int job, mt, nt, slab, x_begin, x_end, n_stages;
+};
+
+__device__ __forceinline__ Unit decode_unit(const TcParams& prm, long long u, int G) {
+  Unit w;
+  w.job = tc_find_job(prm.jobs, prm.n_jobs, u);
+  const TcJob& J = prm.jobs[w.job];
+  long long r = u - J.unit_begin;
+  w.mt = (int)(r % J.m_tiles);
+  r /= J.m_tiles;
+  w.nt = (int)(r % J.n_tiles);
+  w.slab = (int)(r / J.n_tiles);
+  w.x_begin = w.slab * prm.sites_per_slab;
+  w.x_end = min(prm.X, w.x_begin + prm.sites_per_slab);
+  const int groups = (w.x_end - w.x_begin) * prm.n_pairs;
+  w.n_stages = (groups + G - 1) / G;
+  return w;
+}
+
+// Bounded wait by one thread; on timeout raise the CTA abort flag and the status bit.
+__device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t parity,
+                                             volatile int* abort_flag, int* status) {
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(mbar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicOr(status, kStatusTimeout);
+      return false;
+    }
+  }
+}
+
+template <bool TF32, int LEVELS, int NPROD>
+__global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_constant__ TcParams prm) {
+  constexpr int G = TF32 ? 8 : 16;                 // (site, pair) groups per stage
+  constexpr int HALVES = G / 8;                    // 8-group items per row
+  constexpr int STAGES = LEVELS == 3 ? 2 : 3;
+  constexpr int STAGE_BYTES = LEVELS * 2 * (kAPlaneBytes + kBPlaneBytes);
+  // piece products (i, j): leading (0, 0) first, then by increasing i + j
+  constexpr int PI[9] = {0, 0, 1, 1, 0, 2, 1, 2, 2};
+  constexpr int PJ[9] = {0, 1, 0, 1, 2, 0, 2, 1, 2};
+
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
+  __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2], bar_final;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  __shared__ int prod_go, epi_go;
+
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int NC = prm.NC;
+  const int np = prm.n_pairs;
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_acc_full[b]), 1);
+      mbar_init(smem_u32(&bar_acc_empty[b]), 1);
+    }
+    mbar_init(smem_u32(&bar_final), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(&tmem_slot)), "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t smem_base = smem_u32(smem);
+
+  auto a_plane = [&](int stage, int level, int plane) -> uint32_t {
+    return (uint32_t)(stage * STAGE_BYTES + (level * 2 + plane) * kAPlaneBytes);
+  };
+  auto b_plane = [&](int stage, int level, int plane) -> uint32_t {
+    return (uint32_t)(stage * STAGE_BYTES + LEVELS * 2 * kAPlaneBytes +
+                      (level * 2 + plane) * kBPlaneBytes);
+  };
+  auto row_seg = [](int r, int seg) -> uint32_t {
+    return (uint32_t)(((r >> 3) * kSegsPerRow + seg) * 128 + (r & 7) * 16);
+  };
+
+  if (warp >= kProdWarp0) {
+    // ------------------------------------------------------------ producers
+    const int pt = tid - kProdWarp0 * 32;
+    long long s_g = 0;
+    for (long long u = blockIdx.x; u < prm.total_units; u += gridDim.x) {
+      const Unit w = decode_unit(prm, u, G);
+      const TcJob& J = prm.jobs[w.job];
+      const int nd1 = J.nd1, nd2 = J.nd2, nd3 = J.nd3, M = nd1 * nd2, Ntot = prm.P * nd3;
+      const int a_items = kTcM * HALVES, items = a_items + NC * HALVES;
+      bool stop = false;
+      for (int st = 0; st < w.n_stages; ++st, ++s_g) {
+        const int slot = (int)(s_g % STAGES);
+        if (pt == 0) {
+          bool ok = true;
+          if (s_g >= STAGES)
+            ok = wait_bounded(smem_u32(&bar_empty[slot]), (uint32_t)(((s_g / STAGES) + 1) & 1),
+                              &abort_flag, prm.status);
+          prod_go = ok ? 1 : 0;
+        }
+        named_bar(kBarProd, kProdThreads);
+        if (!prod_go) { stop = true; break; }
+        const int g0 = st * G;
+        for (int it = pt; it < items; it += kProdThreads) {
+          float re[3][8], im[3][8];
+          const bool is_a = it < a_items;
+          const int rr = is_a ? it % kTcM : (it - a_items) % NC;
+          const int h = is_a ? it / kTcM : (it - a_items) / NC;
+          if (is_a) {
+            const int m = w.mt * kTcM + rr;
+            const int d1 = m / nd2, d2 = m - d1 * nd2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int gi = g0 + h * 8 + j;
+              const int xl = gi / np, pr = gi - xl * np;
+              const int x = w.x_begin + xl;
+              float2 c0 = make_float2(0.f, 0.f), c1 = c0, c2 = c0;
+              if (m < M && x < w.x_end) {
+                const float2* uq = J.q1[prm.a_slot[pr]] + (size_t)x * 3 * nd1 + d1;
+                const float2* vq = J.q2[prm.b_slot[pr]] + (size_t)x * 3 * nd2 + d2;
+                const float2 u0 = uq[0], u1 = uq[nd1], u2 = uq[2 * nd1];
+                const float2 v0 = vq[0], v1 = vq[nd2], v2 = vq[2 * nd2];
+                const float2 a12 = cmulf(u1, v2), a21 = cmulf(u2, v1);
+                const float2 a20 = cmulf(u2, v0), a02 = cmulf(u0, v2);
+                const float2 a01 = cmulf(u0, v1), a10 = cmulf(u1, v0);
+                c0 = make_float2(a12.x - a21.x, a12.y - a21.y);
+                c1 = make_float2(a20.x - a02.x, a20.y - a02.y);
+                c2 = make_float2(a01.x - a10.x, a01.y - a10.y);
+              }
+              re[0][j] = c0.x; im[0][j] = c0.y;
+              re[1][j] = c1.x; im[1][j] = c1.y;
+              re[2][j] = c2.x; im[2][j] = c2.y;
+            }
+          } else {
+            const int n = w.nt * NC + rr;
+            const int p = n / nd3, d3 = n - p * nd3;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int gi = g0 + h * 8 + j;
+              const int xl = gi / np, pr = gi - xl * np;
+              const int x = w.x_begin + xl;
+              float2 c0 = make_float2(0.f, 0.f), c1 = c0, c2 = c0;
+              if (n < Ntot && x < w.x_end) {
+                const double2 e = prm.phase[(size_t)p * prm.X + x];
+                const float2 ef = make_float2((float)e.x, (float)e.y);
+                const float2* q = J.q3[pr] + (size_t)x * 3 * nd3 + d3;
+                c0 = cmulf(ef, q[0]);
+                c1 = cmulf(ef, q[nd3]);
+                c2 = cmulf(ef, q[2 * nd3]);
+              }
+              re[0][j] = c0.x; im[0][j] = c0.y;
+              re[1][j] = c1.x; im[1][j] = c1.y;
+              re[2][j] = c2.x; im[2][j] = c2.y;
+            }
+          }
+          // colour c occupies K bytes [32c, 32c + 32); this item's 8 groups start at 16h
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int seg = (c * 32 + h * 16) / 16;
+            uint8_t* dr[LEVELS];
+            uint8_t* di[LEVELS];
+#pragma unroll
+            for (int l = 0; l < LEVELS; ++l) {
+              const uint32_t br = is_a ? a_plane(slot, l, 0) : b_plane(slot, l, 0);
+              const uint32_t bi = is_a ? a_plane(slot, l, 1) : b_plane(slot, l, 1);
+              dr[l] = smem + br + row_seg(rr, seg);
+              di[l] = smem + bi + row_seg(rr, seg);
+            }
+            split_store8<TF32, LEVELS>(re[c], dr);
+            split_store8<TF32, LEVELS>(im[c], di);
+          }
+        }
+        fence_async_smem();
+        named_bar(kBarProd, kProdThreads);
+        if (pt == 0) mbar_arrive(smem_u32(&bar_full[slot]));
+      }
+      if (stop) break;
+    }
+  } else if (warp == kMmaWarp) {
+    // ------------------------------------------------------------ MMA issue (one thread)
+    if (lane == 0) {
+      const uint32_t fmt = TF32 ? 2u : 1u;
+      const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) |
+                             ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+      const uint32_t idesc_neg = idesc | (1u << 14);
+      long long s_g = 0, c_g = 0;
+      bool stop = false;
+      for (long long u = blockIdx.x; u < prm.total_units && !stop; u += gridDim.x) {
+        const Unit w = decode_unit(prm, u, G);
+        for (int st = 0; st < w.n_stages; ++st, ++s_g) {
+          const int slot = (int)(s_g % STAGES);
+          const int buf = (int)(c_g & 1);
+          const bool chunk_first = (st % prm.chunk_stages) == 0;
+          const bool chunk_last = (st % prm.chunk_stages) == prm.chunk_stages - 1 ||
+                                  st == w.n_stages - 1;
+          if (chunk_first && c_g >= 2) {
+            if (!wait_bounded(smem_u32(&bar_acc_empty[buf]), (uint32_t)(((c_g >> 1) + 1) & 1),
+                              &abort_flag, prm.status)) { stop = true; break; }
+          }
+          if (!wait_bounded(smem_u32(&bar_full[slot]), (uint32_t)((s_g / STAGES) & 1),
+                            &abort_flag, prm.status)) { stop = true; break; }
+          tc_fence_after();
+          const uint32_t lead_r = tmem + (uint32_t)(buf * 4 * NC);
+          const uint32_t lead_i = lead_r + NC, corr_r = lead_r + 2 * NC, corr_i = lead_r + 3 * NC;
+#pragma unroll
+          for (int ks = 0; ks < 3; ++ks) {
+            const uint32_t kofs = (uint32_t)(ks * 256);
+            const uint32_t first = (chunk_first && ks == 0) ? 0u : 1u;
+#pragma unroll
+            for (int q = 0; q < NPROD; ++q) {
+              const uint64_t ar = smem_desc(smem_base + a_plane(slot, PI[q], 0) + kofs);
+              const uint64_t ai = smem_desc(smem_base + a_plane(slot, PI[q], 1) + kofs);
+              const uint64_t br = smem_desc(smem_base + b_plane(slot, PJ[q], 0) + kofs);
+              const uint64_t bi = smem_desc(smem_base + b_plane(slot, PJ[q], 1) + kofs);
+              const uint32_t dr = q == 0 ? lead_r : corr_r;
+              const uint32_t di = q == 0 ? lead_i : corr_i;
+              const uint32_t acc = (q <= 1) ? first : 1u;
+              mma<TF32>(dr, ar, br, idesc, acc);
+              mma<TF32>(dr, ai, bi, idesc_neg, 1u);
+              mma<TF32>(di, ar, bi, idesc, acc);
+              mma<TF32>(di, ai, br, idesc, 1u);
+            }
+          }
+          tc_commit(smem_u32(&bar_empty[slot]));
+          if (chunk_last) {
+            tc_commit(smem_u32(&bar_acc_full[buf]));
+            ++c_g;
+          }
+        }
+      }
+      tc_commit(smem_u32(&bar_final));
+      wait_bounded(smem_u32(&bar_final), 0u, &abort_flag, prm.status);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue (TMEM lanes)
+    const int row = warp * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t run_r = tmem + lane_base + (uint32_t)(8 * NC);
+    long long c_g = 0;
+    bool stop = false;
+    for (long long u = blockIdx.x; u < prm.total_units && !stop; u += gridDim.x) {
+      const Unit w = decode_unit(prm, u, G);
+      const TcJob& J = prm.jobs[w.job];
+      const int n_chunks = (w.n_stages + prm.chunk_stages - 1) / prm.chunk_stages;
+      for (int ch = 0; ch < n_chunks; ++ch, ++c_g) {
+        const int buf = (int)(c_g & 1);
+        if (tid == 0)
+          epi_go = wait_bounded(smem_u32(&bar_acc_full[buf]), (uint32_t)((c_g >> 1) & 1),
+                                &abort_flag, prm.status) ? 1 : 0;
+        named_bar(kBarEpi, kEpiWarps * 32);
+        if (!epi_go) { stop = true; break; }
+        tc_fence_after();
+        const uint32_t lead = tmem + lane_base + (uint32_t)(buf * 4 * NC);
+        for (int col = 0; col < 2 * NC; col += 16) {
+          float a[16], b[16], r[16];
+          tmem_ld16(lead + col, a);
+          tmem_ld16(lead + 2 * NC + col, b);
+          if (ch > 0) tmem_ld16(run_r + col, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) r[i] = (ch > 0 ? r[i] : 0.f) + (a[i] + b[i]);
+          tmem_st16(run_r + col, r);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        named_bar(kBarEpi, kEpiWarps * 32);
+        if (tid == 0) mbar_arrive(smem_u32(&bar_acc_empty[buf]));
+        if (ch == n_chunks - 1) {
+          // unit done: write the FP32 running sum as this slab's partial block
+          const int m = w.mt * kTcM + row;
+          const int M = J.nd1 * J.nd2, nd3 = J.nd3, Ntot = prm.P * nd3;
+          for (int col = 0; col < NC; col += 16) {
+            float vr[16], vi[16];
+            tmem_ld16(run_r + col, vr);
+            tmem_ld16(run_r + NC + col, vi);
+            tmem_wait_ld();
+            if (m < M) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int n = w.nt * NC + col + i;
+                if (n < Ntot) {
+                  const int p = n / nd3, d3 = n - p * nd3;
+                  J.partial[(((size_t)w.slab * prm.P + p) * M + m) * nd3 + d3] =
+                      make_float2(vr[i], vi[i]);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+
+  // ------------------------------------------------------------ teardown
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+template <bool TF32, int LEVELS, int NPROD>
+cudaError_t launch_form(const TcParams& prm, int grid, cudaStream_t s) {
+  constexpr int STAGES = LEVELS == 3 ? 2 : 3;
+  const size_t smem = (size_t)STAGES * LEVELS * 2 * (kAPlaneBytes + kBPlaneBytes);
+  cudaError_t e = cudaFuncSetAttribute(k_contract_tc<TF32, LEVELS, NPROD>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_contract_tc<TF32, LEVELS, NPROD><<<grid, kTcThreads, smem, s>>>(prm);
+  return cudaGetLastError();
+}
+
+__global__ void k_reduce_slabs_f32(const TcJob* __restrict__ jobs, int n_slab, int P_total) {
+  const TcJob& J = jobs[blockIdx.y];
+  const long long per = (long long)P_total * J.nd1 * J.nd2 * J.nd3;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per;
+       e += (long long)gridDim.x * blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int sl = 0; sl < n_slab; ++sl) {   // fixed order: run-to-run identical
+      const float2 v = J.partial[(size_t)sl * per + e];
+      sr += (double)v.x;
+      si += (double)v.y;
+    }
+    J.B[e] = make_double2(sr, si);
+  }
+}
+
+}  // namespace
+
+int tc_groups_per_stage(int form) { return form == TC_TF32_3 ? 8 : 16; }
+
+cudaError_t launch_contract_tc(const TcParams& prm, int form, int grid, cudaStream_t s) {
+  if (prm.total_units == 0) return cudaSuccess;
+  if (prm.NC < 16 || prm.NC > kMaxNC || prm.NC % 16 != 0 || prm.chunk_stages < 1)
+    return cudaErrorInvalidValue;
+  switch (form) {
+    case TC_BF16_3: return launch_form<false, 2, 3>(prm, grid, s);
+    case TC_BF16_6: return launch_form<false, 3, 6>(prm, grid, s);
+    case TC_BF16_9: return launch_form<false, 3, 9>(prm, grid, s);
+    case TC_TF32_3: return launch_form<true, 2, 3>(prm, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab, int P_total,
+                                    long long max_elems, cudaStream_t s) {
+  if (n_jobs == 0 || max_elems == 0) return cudaSuccess;
+  long long bx = (max_elems + kThreads - 1) / kThreads;
+  if (bx > 4096) bx = 4096;
+  dim3 grid((unsigned)bx, n_jobs);
+  k_reduce_slabs_f32<<<grid, kThreads, 0, s>>>(d_jobs, n_slab, P_total);
+  return cudaGetLastError();
+}
+
+}  // namespace bb
