@@ -136,6 +136,21 @@ size_t bblock_workspace_bytes(const bblock_ctx* ctx);
 /* Number of kernel launches enqueued by the last compute call. */
 int bblock_last_launch_count(const bblock_ctx* ctx);
 
+/* Options of a context (bblock_set_option). The tuning options are the search space of
+ * the tile autotuner; 0 means "chosen automatically". */
+#define BBLOCK_OPT_GRAPHS 1    /* 1 (default): a call repeated with identical arguments is
+                                  captured as a CUDA graph on its second occurrence and
+                                  replayed afterwards; 0: plain launches every time */
+#define BBLOCK_OPT_TC_NC 2     /* tensor-core forms: complex columns per tile, 16, 32 or 48 */
+#define BBLOCK_OPT_TC_CHUNK 3  /* tensor-core forms: stages between accumulator drains, 1..8 */
+#define BBLOCK_OPT_SLABS 4     /* site slabs per job (split of the site sum), 1..4096 */
+
+/* Set an option; BBLOCK_ERR_INVALID_ARG for an unknown option or value. */
+int bblock_set_option(bblock_ctx* ctx, int option, int value);
+
+/* Current value of an option (>= 0), or BBLOCK_ERR_INVALID_ARG. */
+int bblock_get_option(const bblock_ctx* ctx, int option);
+
 /* Per-kernel timing: while enabled, every launch of the library is bracketed by
  * two CUDA events recorded on the launching stream. */
 typedef struct {
@@ -144,7 +159,8 @@ typedef struct {
   double total_ms;  /* summed event-to-event durations of those launches */
 } bblock_kernel_stat;
 
-/* Turn launch timing on (enable != 0) or off. Off by default. */
+/* Turn launch timing on (enable != 0) or off. Off by default. While it is on, calls are
+ * not captured into or replayed from CUDA graphs. */
 int bblock_profile_enable(bblock_ctx* ctx, int enable);
 
 /* Synchronise the recorded events, write up to max_entries per-kernel totals to

@@ -7,4 +7,4 @@ from .bblock import (BblockError, Context, bblock_compute, bblock_compute_batch,
                      bblock_contract_noalloc,
                      bblock_compute_host, bblock_create, bblock_destroy, bblock_last_error,
                      bblock_last_launch_count, bblock_profile_enable,
-                     bblock_profile_read, bblock_status, bblock_workspace_bytes, load)
+                     bblock_profile_read, bblock_set_option, bblock_get_option, bblock_status, bblock_workspace_bytes, load)

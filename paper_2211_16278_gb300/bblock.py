@@ -34,8 +34,9 @@ EXPORTED = (
     "bblock_create", "bblock_destroy", "bblock_last_error", "bblock_status", "bblock_compute",
     "bblock_compute_host", "bblock_compute_batch", "bblock_workspace_bytes",
     "bblock_last_launch_count", "bblock_profile_enable", "bblock_profile_read",
-    "bblock_contract_noalloc",
+    "bblock_contract_noalloc", "bblock_set_option", "bblock_get_option",
 )
+OPTIONS = {"graphs": 1, "tc_nc": 2, "tc_chunk": 3, "slabs": 4}
 
 
 class BblockError(RuntimeError):
@@ -100,6 +101,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bblock_contract_noalloc.argtypes = [I, P, P, P, I, I, I, P, I, P, P, I, P, P,
                                             ctypes.c_char_p, ctypes.c_size_t]
     lib.bblock_contract_noalloc.restype = I
+    lib.bblock_set_option.argtypes = [P, I, I]
+    lib.bblock_set_option.restype = I
+    lib.bblock_get_option.argtypes = [P, I]
+    lib.bblock_get_option.restype = I
     _lib = lib
     return lib
 
@@ -154,6 +159,17 @@ def bblock_workspace_bytes(ctx: Context) -> int:
 
 def bblock_last_launch_count(ctx: Context) -> int:
     return int(load().bblock_last_launch_count(ctx.handle))
+
+
+def bblock_set_option(ctx: Context, option: str, value: int) -> None:
+    """Set a context option: "graphs", "tc_nc", "tc_chunk" or "slabs" (see include/bblock.h)."""
+    _check(ctx, load().bblock_set_option(ctx.handle, OPTIONS[option], int(value)))
+
+
+def bblock_get_option(ctx: Context, option: str) -> int:
+    v = load().bblock_get_option(ctx.handle, OPTIONS[option])
+    _check(ctx, min(v, 0))
+    return int(v)
 
 
 def bblock_profile_enable(ctx: Context, enable: bool = True) -> None:

@@ -45,6 +45,17 @@ struct bblock_ctx {
   std::vector<cudaEvent_t> ev_pool;
   struct Timed { int kind; cudaEvent_t a, b; };
   std::vector<Timed> timed;
+  // options (bblock_set_option)
+  int opt_graphs = 1, opt_tc_nc = 0, opt_tc_chunk = 0, opt_slabs = 0;
+  // CUDA graph of a repeated call: captured on the second call with an identical
+  // signature, replayed while the signature and the buffers it points to stay the same
+  std::vector<uint64_t> last_sig, graph_sig;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_launches = 0;
+  bool capturing = false;
+  char* h_graph_tab = nullptr;
+  size_t h_graph_tab_cap = 0;
+  size_t last_tab_bytes = 0;
 };
 
 namespace {
@@ -66,7 +77,7 @@ cudaEvent_t take_event(bblock_ctx* c) {
 template <class F>
 cudaError_t timed_launch(bblock_ctx* c, int kind, cudaStream_t s, F&& launch) {
   cudaEvent_t a = nullptr, b = nullptr;
-  if (c->prof) {
+  if (c->prof && !c->capturing) {
     a = take_event(c);
     b = take_event(c);
     if (a && b) cudaEventRecord(a, s);
@@ -108,8 +119,16 @@ int cuda_fail(bblock_ctx* c, cudaError_t e, const char* what) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+void drop_graph(bblock_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+  c->graph_sig.clear();
+}
+
 int grow_device(bblock_ctx* c, char** p, size_t* cap, size_t need) {
   if (need <= *cap) return BBLOCK_OK;
+  if (c->capturing) return fail(c, BBLOCK_ERR_UNSUPPORTED, "workspace growth during graph capture");
+  drop_graph(c);  // the graph holds the old addresses
   if (*p) {
     cudaError_t e = cudaStreamSynchronize(c->last_stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize before workspace growth");
@@ -207,6 +226,15 @@ int ensure_phase(bblock_ctx* c, const int32_t* momenta, int n_mom, cudaStream_t 
 
 // Copy `bytes` of host tables into the device table buffer on `s` via the pinned staging buffer.
 int upload_tables(bblock_ctx* c, const void* src, size_t bytes, cudaStream_t s) {
+  c->last_tab_bytes = bytes;
+  if (c->capturing) {
+    // the graph's memcpy node reads this buffer at every replay; it is sized beforehand
+    if (bytes > c->h_graph_tab_cap || bytes > c->tab_cap)
+      return fail(c, BBLOCK_ERR_UNSUPPORTED, "table growth during graph capture");
+    memcpy(c->h_graph_tab, src, bytes);
+    CK(c, cudaMemcpyAsync(c->d_tab, c->h_graph_tab, bytes, cudaMemcpyHostToDevice, s));
+    return BBLOCK_OK;
+  }
   if (c->tab_free) CK(c, cudaEventSynchronize(c->tab_free));  // previous upload has drained
   if (bytes > c->h_tab_cap) {
     if (c->h_tab) cudaFreeHost(c->h_tab);
@@ -305,7 +333,8 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
   const int X = c->X, rows = c->rows, n_ev = c->cfg.n_ev;
   const int form = tc_form_of(c->cfg);
   const int G = tc_groups_per_stage(form);
-  const int chunk_stages = 2;                 // 12 leading accumulations between drains
+  // 12 leading accumulations between drains by default
+  const int chunk_stages = c->opt_tc_chunk > 0 ? c->opt_tc_chunk : 2;
   const int n3_fields = sp.n_pairs * sp.n_coef_sets;
   const int P_launch = per_mom ? 1 : n_mom;
   const int grid_cap = c->num_sms;            // one CTA per SM (all of TMEM, ~200 KB smem)
@@ -330,7 +359,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       ++end;
     }
     const int nj = (int)(end - job_idx);
-    const int NC = choose_nc(jobs, job_idx, end, P_launch);
+    const int NC = c->opt_tc_nc > 0 ? c->opt_tc_nc : choose_nc(jobs, job_idx, end, P_launch);
     long long tiles = 0, max_elems = 0;
     int max_ndf = 0;
     for (size_t k = job_idx; k < end; ++k) {
@@ -339,7 +368,8 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       for (int i = 0; i < 3; ++i) max_ndf = std::max(max_ndf, j.nd[i]);
       max_elems = std::max(max_elems, (long long)P_launch * j.nd[0] * j.nd[1] * j.nd[2]);
     }
-    int n_slab = std::max(min_slabs, choose_slabs(tiles, grid_cap, X, 1, max_slabs));
+    int n_slab = c->opt_slabs > 0 ? std::max(min_slabs, std::min(c->opt_slabs, X))
+                                   : std::max(min_slabs, choose_slabs(tiles, grid_cap, X, 1, max_slabs));
     int sites_per_slab = (X + n_slab - 1) / n_slab;
     n_slab = (X + sites_per_slab - 1) / sites_per_slab;
     size_t ws_need = 0;
@@ -500,7 +530,8 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       for (int i = 0; i < 3; ++i) max_ndf = std::max(max_ndf, j.nd[i]);
       max_elems = std::max(max_elems, (long long)n_mom * j.nd[0] * j.nd[1] * j.nd[2]);
     }
-    int n_slab = choose_slabs(tiles, ctas, X, xc, max_slabs);
+    int n_slab = c->opt_slabs > 0 ? std::min(c->opt_slabs, (X + xc - 1) / xc)
+                                   : choose_slabs(tiles, ctas, X, xc, max_slabs);
     int sites_per_slab = (X + n_slab - 1) / n_slab;
     sites_per_slab = (sites_per_slab + xc - 1) / xc * xc;
     n_slab = (X + sites_per_slab - 1) / sites_per_slab;
@@ -621,6 +652,100 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
   return BBLOCK_OK;
 }
 
+// Everything a call's launch sequence depends on, as a flat key.
+std::vector<uint64_t> call_signature(const bblock_ctx* c, const std::vector<JobIn>& jobs,
+                                     const int32_t* momenta, int n_mom, const int32_t* spin_idx,
+                                     const double* coeffs, int n_spin, int per_mom) {
+  std::vector<uint64_t> k;
+  k.reserve(16 + jobs.size() * 8 + 3 * n_mom + 3 * n_spin);
+  k.push_back((uint64_t)c->cfg.precision | ((uint64_t)c->cfg.bf16_products << 8) |
+              ((uint64_t)per_mom << 16) | ((uint64_t)c->opt_tc_nc << 24) |
+              ((uint64_t)c->opt_tc_chunk << 32) | ((uint64_t)c->opt_slabs << 40));
+  k.push_back((uint64_t)n_mom | ((uint64_t)n_spin << 32));
+  for (int i = 0; i < 3 * n_mom; ++i) k.push_back((uint64_t)(uint32_t)momenta[i]);
+  for (int i = 0; i < 3 * n_spin; ++i) k.push_back((uint64_t)(uint32_t)spin_idx[i]);
+  const int n_coef = 2 * n_spin * (per_mom ? n_mom : 1);
+  for (int i = 0; i < n_coef; ++i) {
+    uint64_t b;
+    memcpy(&b, &coeffs[i], sizeof(b));
+    k.push_back(b);
+  }
+  for (const JobIn& j : jobs) {
+    k.push_back(reinterpret_cast<uint64_t>(j.V));
+    for (int i = 0; i < 3; ++i) k.push_back(reinterpret_cast<uint64_t>(j.phi[i]));
+    k.push_back(reinterpret_cast<uint64_t>(j.B));
+    k.push_back((uint64_t)j.nd[0] | ((uint64_t)j.nd[1] << 20) | ((uint64_t)j.nd[2] << 40));
+  }
+  return k;
+}
+
+// run_jobs with CUDA-graph reuse: the second call with an identical signature is captured
+// (thread-local capture mode) and every later identical call replays the graph.
+int run_jobs_cached(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momenta,
+                    int n_mom, const int32_t* spin_idx, const double* coeffs, int n_spin,
+                    int per_mom, cudaStream_t s) {
+  if (!c->opt_graphs || c->prof || jobs.empty() || n_mom == 0)
+    return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
+  std::vector<uint64_t> sig = call_signature(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin,
+                                             per_mom);
+  if (c->graph_exec && sig == c->graph_sig) {
+    CK(c, cudaSetDevice(c->cfg.device));
+    int rc = ensure_phase(c, momenta, n_mom, s);   // a call in between may have replaced it
+    if (rc) return rc;
+    if (!c->graph_exec) return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
+    CK(c, cudaGraphLaunch(c->graph_exec, s));
+    c->last_launches = c->graph_launches;
+    c->last_stream = s;
+    return BBLOCK_OK;
+  }
+  if (sig != c->last_sig) {
+    c->last_sig = sig;
+    return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
+  }
+  // second identical call: every buffer already has its size, so capture it
+  drop_graph(c);
+  if (c->h_graph_tab_cap < c->last_tab_bytes) {
+    if (c->h_graph_tab) cudaFreeHost(c->h_graph_tab);
+    c->h_graph_tab = nullptr;
+    c->h_graph_tab_cap = 0;
+    if (cudaHostAlloc(&c->h_graph_tab, c->last_tab_bytes, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
+    }
+    c->h_graph_tab_cap = c->last_tab_bytes;
+  }
+  CK(c, cudaSetDevice(c->cfg.device));
+  // the previous plain upload must have drained before the capture reuses the device tables
+  if (c->tab_free) CK(c, cudaEventSynchronize(c->tab_free));
+  CK(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  c->capturing = true;
+  int rc = run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
+  c->capturing = false;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (rc != BBLOCK_OK || e != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    c->last_sig.clear();
+    c->err.clear();
+    return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->last_sig.clear();
+    return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
+  }
+  c->graph_exec = exec;
+  c->graph_sig = sig;
+  c->graph_launches = c->last_launches;
+  CK(c, cudaGraphLaunch(exec, s));
+  c->last_stream = s;
+  return BBLOCK_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -674,6 +799,8 @@ void bblock_destroy(bblock_ctx* c) {
   cudaFree(c->d_io);
   if (c->h_tab) cudaFreeHost(c->h_tab);
   if (c->tab_free) cudaEventDestroy(c->tab_free);
+  drop_graph(c);
+  if (c->h_graph_tab) cudaFreeHost(c->h_graph_tab);
   for (auto& t : c->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   cudaGetLastError();
@@ -724,7 +851,7 @@ int bblock_compute(bblock_ctx* c, int n_t, const void* V, const void* phi1, cons
       if (rc) return rc;
     }
   }
-  return run_jobs(c, jobs, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom,
+  return run_jobs_cached(c, jobs, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom,
                   static_cast<cudaStream_t>(stream));
 }
 
@@ -752,7 +879,7 @@ int bblock_compute_batch(bblock_ctx* c, const bblock_job* jobs_in, int n_jobs,
   std::stable_sort(jobs.begin(), jobs.end(), [](const JobIn& a, const JobIn& b) {
     return (long long)a.nd[0] * a.nd[1] * a.nd[2] > (long long)b.nd[0] * b.nd[1] * b.nd[2];
   });
-  return run_jobs(c, jobs, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom,
+  return run_jobs_cached(c, jobs, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom,
                   static_cast<cudaStream_t>(stream));
 }
 
@@ -801,6 +928,43 @@ size_t bblock_workspace_bytes(const bblock_ctx* c) {
 }
 
 int bblock_last_launch_count(const bblock_ctx* c) { return c ? c->last_launches : 0; }
+
+int bblock_set_option(bblock_ctx* c, int option, int value) {
+  if (!c) return BBLOCK_ERR_INVALID_ARG;
+  switch (option) {
+    case BBLOCK_OPT_GRAPHS:
+      if (value != 0 && value != 1) break;
+      c->opt_graphs = value;
+      if (!value) drop_graph(c);
+      return BBLOCK_OK;
+    case BBLOCK_OPT_TC_NC:
+      if (value != 0 && value != 16 && value != 32 && value != 48) break;
+      c->opt_tc_nc = value;
+      return BBLOCK_OK;
+    case BBLOCK_OPT_TC_CHUNK:
+      if (value < 0 || value > 8) break;
+      c->opt_tc_chunk = value;
+      return BBLOCK_OK;
+    case BBLOCK_OPT_SLABS:
+      if (value < 0 || value > 4096) break;
+      c->opt_slabs = value;
+      return BBLOCK_OK;
+    default:
+      break;
+  }
+  return fail(c, BBLOCK_ERR_INVALID_ARG, "option %d does not take the value %d", option, value);
+}
+
+int bblock_get_option(const bblock_ctx* c, int option) {
+  if (!c) return BBLOCK_ERR_INVALID_ARG;
+  switch (option) {
+    case BBLOCK_OPT_GRAPHS: return c->opt_graphs;
+    case BBLOCK_OPT_TC_NC: return c->opt_tc_nc;
+    case BBLOCK_OPT_TC_CHUNK: return c->opt_tc_chunk;
+    case BBLOCK_OPT_SLABS: return c->opt_slabs;
+    default: return BBLOCK_ERR_INVALID_ARG;
+  }
+}
 
 int bblock_profile_enable(bblock_ctx* c, int enable) {
   if (!c) return BBLOCK_ERR_INVALID_ARG;

@@ -16,9 +16,11 @@
 // second accumulator. Each work unit (job, 128 pairs, NC columns, site slab) writes its
 // running sum as an FP32 partial block; the slab partials are summed in FP64 in index order.
 //
-// Warp roles (13 warps): 0-3 epilogue (TMEM lanes 0-127: drains, partial write-out),
-// 4 MMA issue + TMEM allocation, 5-12 operand producers. Every wait is bounded; on a
-// timeout the CTA sets a status bit, stops, waits (bounded) for its MMAs and frees TMEM.
+// Warp roles: 0-3 epilogue (TMEM lanes 0-127: drains, partial write-out), 4 MMA issue and
+// TMEM allocation, 5.. operand producers (11 warps for BF16, 6 for TF32). Every wait is
+// bounded; on a timeout the CTA raises an abort flag and a status bit, the roles run out
+// their loops without waiting or computing, the MMA thread waits (bounded) for its
+// outstanding MMAs and the allocating warp frees TMEM.
 #include <cuda_bf16.h>
 #include <cstdint>
 
@@ -31,10 +33,16 @@ constexpr int kTcM = 128;
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;
 constexpr int kProdWarp0 = 5;
-constexpr int kProdWarps = 8;
-constexpr int kTcThreads = (kProdWarp0 + kProdWarps) * 32;
-constexpr int kProdThreads = kProdWarps * 32;
 constexpr int kTmemCols = 512;
+// Producer warps: one 8-group item per thread. BF16 stages hold 16 groups (two halves per
+// row): 8 warps build the 128-row diquark tile, 3 warps the <= 48-row third-quark tile.
+// TF32 stages hold 8 groups: 4 + 2 warps.
+template <bool TF32> struct Roles {
+  static constexpr int kAThreads = TF32 ? 128 : 256;
+  static constexpr int kBThreads = TF32 ? 64 : 96;
+  static constexpr int kProdThreads = kAThreads + kBThreads;
+  static constexpr int kThreads = kProdWarp0 * 32 + kProdThreads;
+};
 constexpr int kMaxNC = 48;
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s
 constexpr int kBarProd = 1, kBarEpi = 2;
@@ -139,6 +147,11 @@ __device__ __forceinline__ float tf32_round(float v) {
 
 // Split 8 FP32 values into LEVELS pieces and store each piece's 8 values as one K run of
 // a core-matrix row (16 bytes of BF16, or 32 bytes = two 16-byte rows of TF32).
+// BF16: the pieces are successive truncations to the top 8 significant bits,
+//   v0 = trunc8(v), v1 = trunc8(v - v0), v2 = (v - v0) - v1,
+// every subtraction is exact and v2 has at most 8 significant bits, so v0 + v1 + v2 == v;
+// with two pieces the second is rounded to nearest (error <= 2^-17 |v|).
+// TF32: v0 = trunc11(v), v1 = rn_tf32(v - v0) (error <= 2^-21 |v|).
 template <bool TF32, int LEVELS>
 __device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const (&dst)[LEVELS]) {
   if (!TF32) {
@@ -147,33 +160,38 @@ __device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const
     for (int i = 0; i < 8; ++i) r[i] = v[i];
 #pragma unroll
     for (int l = 0; l < LEVELS; ++l) {
-      uint32_t w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(r[2 * i], r[2 * i + 1]);
-        const float2 back = __bfloat1622float2(h);
-        r[2 * i] -= back.x;
-        r[2 * i + 1] -= back.y;
-        w[i] = *reinterpret_cast<uint32_t*>(&h);
-      }
-      *reinterpret_cast<uint4*>(dst[l]) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-  } else {
-    float r[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) r[i] = v[i];
-#pragma unroll
-    for (int l = 0; l < LEVELS; ++l) {
-      float h[8];
+      uint32_t piece[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        h[i] = tf32_round(r[i]);
-        r[i] -= h[i];
+        if (l < LEVELS - 1) {
+          piece[i] = __float_as_uint(r[i]) & 0xFFFF0000u;
+          r[i] -= __uint_as_float(piece[i]);
+        } else if (LEVELS == 3) {
+          piece[i] = __float_as_uint(r[i]);       // exact in BF16
+        } else {
+          const __nv_bfloat16 h = __float2bfloat16_rn(r[i]);
+          piece[i] = (uint32_t)(*reinterpret_cast<const uint16_t*>(&h)) << 16;
+        }
       }
-      // a 32-byte K run spans two adjacent core matrices along K (128 bytes apart)
-      *reinterpret_cast<float4*>(dst[l]) = make_float4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<float4*>(dst[l] + 128) = make_float4(h[4], h[5], h[6], h[7]);
+      uint4 w;
+      w.x = __byte_perm(piece[0], piece[1], 0x7632);
+      w.y = __byte_perm(piece[2], piece[3], 0x7632);
+      w.z = __byte_perm(piece[4], piece[5], 0x7632);
+      w.w = __byte_perm(piece[6], piece[7], 0x7632);
+      *reinterpret_cast<uint4*>(dst[l]) = w;
     }
+  } else {
+    float h[8], lo[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i] = __uint_as_float(__float_as_uint(v[i]) & 0xFFFFE000u);
+      lo[i] = tf32_round(v[i] - h[i]);
+    }
+    // a 32-byte K run spans two adjacent core matrices along K (128 bytes apart)
+    *reinterpret_cast<float4*>(dst[0]) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(dst[0] + 128) = make_float4(h[4], h[5], h[6], h[7]);
+    *reinterpret_cast<float4*>(dst[1]) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<float4*>(dst[1] + 128) = make_float4(lo[4], lo[5], lo[6], lo[7]);
   }
 }
 
@@ -226,9 +244,10 @@ __device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t parity,
 }
 
 template <bool TF32, int LEVELS, int NPROD>
-__global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_constant__ TcParams prm) {
+__global__ void __launch_bounds__(Roles<TF32>::kThreads, 1)
+k_contract_tc(const __grid_constant__ TcParams prm) {
+  using R = Roles<TF32>;
   constexpr int G = TF32 ? 8 : 16;                 // (site, pair) groups per stage
-  constexpr int HALVES = G / 8;                    // 8-group items per row
   constexpr int STAGES = LEVELS == 3 ? 2 : 3;
   constexpr int STAGE_BYTES = LEVELS * 2 * (kAPlaneBytes + kBPlaneBytes);
   // piece products (i, j): leading (0, 0) first, then by increasing i + j
@@ -240,7 +259,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
   __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2], bar_final;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
-  __shared__ int prod_go, epi_go;
+  // per-unit field pointers of every spin pair
+  __shared__ const float2* s_q1[kMaxPairs];
+  __shared__ const float2* s_q2[kMaxPairs];
+  __shared__ const float2* s_q3[kMaxPairs];
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int NC = prm.NC;
@@ -283,100 +305,118 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
 
   if (warp >= kProdWarp0) {
     // ------------------------------------------------------------ producers
+    // Thread roles are fixed: pt < kAThreads builds diquark rows, the rest build third-quark
+    // rows; each thread owns one row and 8 consecutive groups (half h) of every stage.
     const int pt = tid - kProdWarp0 * 32;
+    const bool is_a = pt < R::kAThreads;
+    const int rr = is_a ? pt % kTcM : (pt - R::kAThreads) % kMaxNC;
+    const int h = is_a ? pt / kTcM : (pt - R::kAThreads) / kMaxNC;
+    const bool row_used = is_a || (rr < NC && h < G / 8);
     long long s_g = 0;
     for (long long u = blockIdx.x; u < prm.total_units; u += gridDim.x) {
       const Unit w = decode_unit(prm, u, G);
       const TcJob& J = prm.jobs[w.job];
-      const int nd1 = J.nd1, nd2 = J.nd2, nd3 = J.nd3, M = nd1 * nd2, Ntot = prm.P * nd3;
-      const int a_items = kTcM * HALVES, items = a_items + NC * HALVES;
-      bool stop = false;
+      const int nd1 = J.nd1, nd2 = J.nd2, nd3 = J.nd3;
+      // per-unit constants of this thread's row
+      bool row_ok;
+      int off1 = 0, off2 = 0, s1 = 0, s2 = 0, pidx = 0;
+      if (is_a) {
+        const int m = w.mt * kTcM + rr;
+        row_ok = m < nd1 * nd2;
+        const int d1 = row_ok ? m / nd2 : 0, d2 = row_ok ? m - d1 * nd2 : 0;
+        off1 = d1; off2 = d2; s1 = nd1; s2 = nd2;
+      } else {
+        const int n = w.nt * NC + rr;
+        row_ok = row_used && n < prm.P * nd3;
+        const int p = row_ok ? n / nd3 : 0, d3 = row_ok ? n - p * nd3 : 0;
+        off1 = d3; s1 = nd3; pidx = p;
+      }
+      // all producers have passed the previous unit's last stage barrier, so the pointer
+      // table can be rewritten; the barrier below publishes it
+      if (pt < np) {
+        s_q1[pt] = J.q1[prm.a_slot[pt]];
+        s_q2[pt] = J.q2[prm.b_slot[pt]];
+        s_q3[pt] = J.q3[pt];
+      }
+      named_bar(kBarProd, R::kProdThreads);
+      const double2* phase_p = prm.phase + (size_t)pidx * prm.X;
       for (int st = 0; st < w.n_stages; ++st, ++s_g) {
         const int slot = (int)(s_g % STAGES);
-        if (pt == 0) {
-          bool ok = true;
-          if (s_g >= STAGES)
-            ok = wait_bounded(smem_u32(&bar_empty[slot]), (uint32_t)(((s_g / STAGES) + 1) & 1),
-                              &abort_flag, prm.status);
-          prod_go = ok ? 1 : 0;
-        }
-        named_bar(kBarProd, kProdThreads);
-        if (!prod_go) { stop = true; break; }
-        const int g0 = st * G;
-        for (int it = pt; it < items; it += kProdThreads) {
+        bool ok = !abort_flag;
+        if (ok && s_g >= STAGES)
+          ok = wait_bounded(smem_u32(&bar_empty[slot]), (uint32_t)(((s_g / STAGES) + 1) & 1),
+                            &abort_flag, prm.status);
+        if (ok && row_used) {
           float re[3][8], im[3][8];
-          const bool is_a = it < a_items;
-          const int rr = is_a ? it % kTcM : (it - a_items) % NC;
-          const int h = is_a ? it / kTcM : (it - a_items) / NC;
-          if (is_a) {
-            const int m = w.mt * kTcM + rr;
-            const int d1 = m / nd2, d2 = m - d1 * nd2;
+          // first group of this thread's run of 8
+          const int gi0 = st * G + h * 8;
+          int xl = gi0 / np, pr = gi0 - xl * np;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int gi = g0 + h * 8 + j;
-              const int xl = gi / np, pr = gi - xl * np;
+          for (int half = 0; half < 2; ++half) {
+            // 4 groups: issue every load first, then compute
+            float2 ld[4][6];
+            bool vld[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
               const int x = w.x_begin + xl;
-              float2 c0 = make_float2(0.f, 0.f), c1 = c0, c2 = c0;
-              if (m < M && x < w.x_end) {
-                const float2* uq = J.q1[prm.a_slot[pr]] + (size_t)x * 3 * nd1 + d1;
-                const float2* vq = J.q2[prm.b_slot[pr]] + (size_t)x * 3 * nd2 + d2;
-                const float2 u0 = uq[0], u1 = uq[nd1], u2 = uq[2 * nd1];
-                const float2 v0 = vq[0], v1 = vq[nd2], v2 = vq[2 * nd2];
+              vld[j] = row_ok && x < w.x_end;
+              const int xs = vld[j] ? x : w.x_begin;
+              if (is_a) {
+                const float2* uq = s_q1[pr] + (size_t)xs * 3 * s1 + off1;
+                const float2* vq = s_q2[pr] + (size_t)xs * 3 * s2 + off2;
+                ld[j][0] = uq[0]; ld[j][1] = uq[s1]; ld[j][2] = uq[2 * s1];
+                ld[j][3] = vq[0]; ld[j][4] = vq[s2]; ld[j][5] = vq[2 * s2];
+              } else {
+                const float2* q = s_q3[pr] + (size_t)xs * 3 * s1 + off1;
+                const double2 e = phase_p[xs];
+                ld[j][0] = q[0]; ld[j][1] = q[s1]; ld[j][2] = q[2 * s1];
+                ld[j][3] = make_float2((float)e.x, (float)e.y);
+              }
+              if (++pr == np) { pr = 0; ++xl; }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              float2 c0, c1, c2;
+              if (is_a) {
+                const float2 u0 = ld[j][0], u1 = ld[j][1], u2 = ld[j][2];
+                const float2 v0 = ld[j][3], v1 = ld[j][4], v2 = ld[j][5];
                 const float2 a12 = cmulf(u1, v2), a21 = cmulf(u2, v1);
                 const float2 a20 = cmulf(u2, v0), a02 = cmulf(u0, v2);
                 const float2 a01 = cmulf(u0, v1), a10 = cmulf(u1, v0);
                 c0 = make_float2(a12.x - a21.x, a12.y - a21.y);
                 c1 = make_float2(a20.x - a02.x, a20.y - a02.y);
                 c2 = make_float2(a01.x - a10.x, a01.y - a10.y);
+              } else {
+                c0 = cmulf(ld[j][3], ld[j][0]);
+                c1 = cmulf(ld[j][3], ld[j][1]);
+                c2 = cmulf(ld[j][3], ld[j][2]);
               }
-              re[0][j] = c0.x; im[0][j] = c0.y;
-              re[1][j] = c1.x; im[1][j] = c1.y;
-              re[2][j] = c2.x; im[2][j] = c2.y;
-            }
-          } else {
-            const int n = w.nt * NC + rr;
-            const int p = n / nd3, d3 = n - p * nd3;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int gi = g0 + h * 8 + j;
-              const int xl = gi / np, pr = gi - xl * np;
-              const int x = w.x_begin + xl;
-              float2 c0 = make_float2(0.f, 0.f), c1 = c0, c2 = c0;
-              if (n < Ntot && x < w.x_end) {
-                const double2 e = prm.phase[(size_t)p * prm.X + x];
-                const float2 ef = make_float2((float)e.x, (float)e.y);
-                const float2* q = J.q3[pr] + (size_t)x * 3 * nd3 + d3;
-                c0 = cmulf(ef, q[0]);
-                c1 = cmulf(ef, q[nd3]);
-                c2 = cmulf(ef, q[2 * nd3]);
-              }
-              re[0][j] = c0.x; im[0][j] = c0.y;
-              re[1][j] = c1.x; im[1][j] = c1.y;
-              re[2][j] = c2.x; im[2][j] = c2.y;
+              const float z = vld[j] ? 1.f : 0.f;
+              const int jj = half * 4 + j;
+              re[0][jj] = c0.x * z; im[0][jj] = c0.y * z;
+              re[1][jj] = c1.x * z; im[1][jj] = c1.y * z;
+              re[2][jj] = c2.x * z; im[2][jj] = c2.y * z;
             }
           }
-          // colour c occupies K bytes [32c, 32c + 32); this item's 8 groups start at 16h
+          // colour c occupies K bytes [32c, 32c + 32); this thread's 8 groups start at 16h
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const int seg = (c * 32 + h * 16) / 16;
+            const int seg = 2 * c + h;
             uint8_t* dr[LEVELS];
             uint8_t* di[LEVELS];
 #pragma unroll
             for (int l = 0; l < LEVELS; ++l) {
-              const uint32_t br = is_a ? a_plane(slot, l, 0) : b_plane(slot, l, 0);
-              const uint32_t bi = is_a ? a_plane(slot, l, 1) : b_plane(slot, l, 1);
-              dr[l] = smem + br + row_seg(rr, seg);
-              di[l] = smem + bi + row_seg(rr, seg);
+              dr[l] = smem + (is_a ? a_plane(slot, l, 0) : b_plane(slot, l, 0)) + row_seg(rr, seg);
+              di[l] = smem + (is_a ? a_plane(slot, l, 1) : b_plane(slot, l, 1)) + row_seg(rr, seg);
             }
             split_store8<TF32, LEVELS>(re[c], dr);
             split_store8<TF32, LEVELS>(im[c], di);
           }
         }
         fence_async_smem();
-        named_bar(kBarProd, kProdThreads);
+        named_bar(kBarProd, R::kProdThreads);
         if (pt == 0) mbar_arrive(smem_u32(&bar_full[slot]));
       }
-      if (stop) break;
     }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issue (one thread)
@@ -404,16 +444,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
           tc_fence_after();
           const uint32_t lead_r = tmem + (uint32_t)(buf * 4 * NC);
           const uint32_t lead_i = lead_r + NC, corr_r = lead_r + 2 * NC, corr_i = lead_r + 3 * NC;
+          const uint32_t sa = smem_base + (uint32_t)(slot * STAGE_BYTES);
+          const uint32_t sb = sa + LEVELS * 2 * kAPlaneBytes;
 #pragma unroll
           for (int ks = 0; ks < 3; ++ks) {
             const uint32_t kofs = (uint32_t)(ks * 256);
             const uint32_t first = (chunk_first && ks == 0) ? 0u : 1u;
 #pragma unroll
             for (int q = 0; q < NPROD; ++q) {
-              const uint64_t ar = smem_desc(smem_base + a_plane(slot, PI[q], 0) + kofs);
-              const uint64_t ai = smem_desc(smem_base + a_plane(slot, PI[q], 1) + kofs);
-              const uint64_t br = smem_desc(smem_base + b_plane(slot, PJ[q], 0) + kofs);
-              const uint64_t bi = smem_desc(smem_base + b_plane(slot, PJ[q], 1) + kofs);
+              const uint64_t ar = smem_desc(sa + (PI[q] * 2 + 0) * kAPlaneBytes + kofs);
+              const uint64_t ai = smem_desc(sa + (PI[q] * 2 + 1) * kAPlaneBytes + kofs);
+              const uint64_t br = smem_desc(sb + (PJ[q] * 2 + 0) * kBPlaneBytes + kofs);
+              const uint64_t bi = smem_desc(sb + (PJ[q] * 2 + 1) * kBPlaneBytes + kofs);
               const uint32_t dr = q == 0 ? lead_r : corr_r;
               const uint32_t di = q == 0 ? lead_i : corr_i;
               const uint32_t acc = (q <= 1) ? first : 1u;
@@ -440,35 +482,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc(const __grid_cons
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const uint32_t run_r = tmem + lane_base + (uint32_t)(8 * NC);
     long long c_g = 0;
-    bool stop = false;
-    for (long long u = blockIdx.x; u < prm.total_units && !stop; u += gridDim.x) {
+    for (long long u = blockIdx.x; u < prm.total_units; u += gridDim.x) {
       const Unit w = decode_unit(prm, u, G);
       const TcJob& J = prm.jobs[w.job];
       const int n_chunks = (w.n_stages + prm.chunk_stages - 1) / prm.chunk_stages;
       for (int ch = 0; ch < n_chunks; ++ch, ++c_g) {
         const int buf = (int)(c_g & 1);
-        if (tid == 0)
-          epi_go = wait_bounded(smem_u32(&bar_acc_full[buf]), (uint32_t)((c_g >> 1) & 1),
-                                &abort_flag, prm.status) ? 1 : 0;
-        named_bar(kBarEpi, kEpiWarps * 32);
-        if (!epi_go) { stop = true; break; }
-        tc_fence_after();
-        const uint32_t lead = tmem + lane_base + (uint32_t)(buf * 4 * NC);
-        for (int col = 0; col < 2 * NC; col += 16) {
-          float a[16], b[16], r[16];
-          tmem_ld16(lead + col, a);
-          tmem_ld16(lead + 2 * NC + col, b);
-          if (ch > 0) tmem_ld16(run_r + col, r);
-          tmem_wait_ld();
+        bool ok = !abort_flag;
+        if (ok)
+          ok = wait_bounded(smem_u32(&bar_acc_full[buf]), (uint32_t)((c_g >> 1) & 1),
+                            &abort_flag, prm.status);
+        // the TMEM loads below are warp-collective: decide per warp
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok) {
+          tc_fence_after();
+          const uint32_t lead = tmem + lane_base + (uint32_t)(buf * 4 * NC);
+          for (int col = 0; col < 2 * NC; col += 16) {
+            float a[16], b[16], r[16];
+            tmem_ld16(lead + col, a);
+            tmem_ld16(lead + 2 * NC + col, b);
+            if (ch > 0) tmem_ld16(run_r + col, r);
+            tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 16; ++i) r[i] = (ch > 0 ? r[i] : 0.f) + (a[i] + b[i]);
-          tmem_st16(run_r + col, r);
+            for (int i = 0; i < 16; ++i) r[i] = (ch > 0 ? r[i] : 0.f) + (a[i] + b[i]);
+            tmem_st16(run_r + col, r);
+          }
+          tmem_wait_st();
         }
-        tmem_wait_st();
         tc_fence_before();
         named_bar(kBarEpi, kEpiWarps * 32);
         if (tid == 0) mbar_arrive(smem_u32(&bar_acc_empty[buf]));
-        if (ch == n_chunks - 1) {
+        if (ok && ch == n_chunks - 1) {
           // unit done: write the FP32 running sum as this slab's partial block
           const int m = w.mt * kTcM + row;
           const int M = J.nd1 * J.nd2, nd3 = J.nd3, Ntot = prm.P * nd3;
@@ -511,7 +555,7 @@ cudaError_t launch_form(const TcParams& prm, int grid, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_contract_tc<TF32, LEVELS, NPROD>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_contract_tc<TF32, LEVELS, NPROD><<<grid, kTcThreads, smem, s>>>(prm);
+  k_contract_tc<TF32, LEVELS, NPROD><<<grid, Roles<TF32>::kThreads, smem, s>>>(prm);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,103 @@
+"""CUDA-graph replay of repeated calls and the tuning options, through the C ABI.
+
+A call repeated with identical arguments is captured as a CUDA graph on its second
+occurrence and replayed afterwards; the replayed blocks must be bitwise equal to the plain
+launches, and any change of arguments must fall back to plain launches. The tile options
+(N tile, drain interval, slab count) change only how the work is cut, so every setting must
+stay within the form's tolerance of the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2211_16278_gb300 as bb
+    bb.load()
+    return torch, bb
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def setup(torch, inp):
+    dev = torch.device("cuda:0")
+    return (torch.from_numpy(inp.V).to(dev), [torch.from_numpy(inp.phi[0][i]).to(dev) for i in range(3)])
+
+
+@pytest.mark.parametrize("precision,products", [("fp64", 6), ("bf16", 6), ("tf32x3", 6)])
+def test_graph_replay_is_bitwise_equal_to_plain_launches(env, precision, products):
+    torch, bb = env
+    inp = workloads.custom(4, 10, (9, 8, 12), 2, [(0, 0, 0), (1, 0, 0), (1, 1, 0)],
+                           [(0, 1, 0), (1, 0, 0), (2, 3, 2)], [0.7, -0.7, 0.7], seed=3000)
+    V, phis = setup(torch, inp)
+    plain = bb.bblock_create(4, 10, 12, precision, bf16_products=products)
+    bb.bblock_set_option(plain, "graphs", 0)
+    ref = bb.bblock_compute(plain, V, *phis, inp.momenta, inp.spins, inp.coeffs).cpu().numpy()
+    n_plain = bb.bblock_last_launch_count(plain)
+    ctx = bb.bblock_create(4, 10, 12, precision, bf16_products=products)
+    assert bb.bblock_get_option(ctx, "graphs") == 1
+    B = torch.empty_like(torch.from_numpy(ref)).to("cuda:0")
+    for call in range(4):          # plain, capture + replay, replay, replay
+        B.zero_()
+        bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B)
+        bb.bblock_status(ctx)
+        assert np.array_equal(B.cpu().numpy(), ref), f"call {call}"
+        assert bb.bblock_last_launch_count(ctx) == n_plain
+    # the inputs change in place: a replay reads them afresh
+    phis[0].mul_(2.0)
+    bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B)
+    bb.bblock_status(ctx)
+    assert np.allclose(B.cpu().numpy(), 2.0 * ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    # different arguments (another output buffer, other momenta) fall back to plain launches
+    B2 = torch.zeros_like(B)
+    bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B2)
+    mom2 = inp.momenta[:2]
+    B3 = bb.bblock_compute(ctx, V, *phis, mom2, inp.spins, inp.coeffs)
+    bb.bblock_status(ctx)
+    assert np.array_equal(B2.cpu().numpy(), B.cpu().numpy())
+    assert np.array_equal(B3.cpu().numpy(), B.cpu().numpy()[:, :2])
+    bb.bblock_destroy(ctx)
+    bb.bblock_destroy(plain)
+
+
+@pytest.mark.parametrize("nc,chunk,slabs", [(16, 1, 0), (32, 3, 0), (48, 2, 5), (0, 4, 1), (0, 0, 17)])
+def test_tile_options_keep_parity(env, nc, chunk, slabs):
+    torch, bb = env
+    inp = workloads.custom(5, 12, (12, 11, 13), 1, [(0, 0, 0), (1, 0, 0), (1, 1, 0)],
+                           [(0, 1, 0), (1, 0, 0), (2, 3, 2)], [0.7, -0.7, 0.7], seed=3100)
+    V, phis = setup(torch, inp)
+    ref = oracle.bblock(5, inp.V[0], *[inp.phi[0][i][0] for i in range(3)], inp.momenta,
+                        inp.spins, inp.coeffs)
+    ctx = bb.bblock_create(5, 12, 13, "bf16", bf16_products=6)
+    bb.bblock_set_option(ctx, "tc_nc", nc)
+    bb.bblock_set_option(ctx, "tc_chunk", chunk)
+    bb.bblock_set_option(ctx, "slabs", slabs)
+    B = bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs)
+    bb.bblock_status(ctx)
+    assert rel(B.cpu().numpy()[0], ref) <= 1e-6
+    bb.bblock_destroy(ctx)
+    ctx = bb.bblock_create(5, 12, 13, "fp64")
+    bb.bblock_set_option(ctx, "slabs", slabs)
+    B = bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs)
+    bb.bblock_status(ctx)
+    assert rel(B.cpu().numpy()[0], ref) <= 1e-12
+    bb.bblock_destroy(ctx)
+
+
+def test_bad_option_values_are_rejected(env):
+    torch, bb = env
+    ctx = bb.bblock_create(2, 4, 4, "fp64")
+    for opt, val in (("tc_nc", 40), ("tc_chunk", 9), ("graphs", 2), ("slabs", -1)):
+        with pytest.raises(bb.BblockError, match="INVALID_ARG"):
+            bb.bblock_set_option(ctx, opt, val)
+    bb.bblock_destroy(ctx)
