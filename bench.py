@@ -268,7 +268,9 @@ def run_ours(args):
     n_alpha, n_beta, pairs = spin_structure(inp.spins)
     V = torch.from_numpy(inp.V).to(dev)
     phis = [torch.from_numpy(inp.phi[0][i]).to(dev) for i in range(3)]
-    stream = torch.cuda.current_stream(dev)
+    # a created stream: repeated calls are then replayed from a CUDA graph by the library
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
     blocks_per_step = w.n_t * P
 
     def measure(precision, products, sampler=None):

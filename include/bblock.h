@@ -138,9 +138,10 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 
 /* Options of a context (bblock_set_option). The tuning options are the search space of
  * the tile autotuner; 0 means "chosen automatically". */
-#define BBLOCK_OPT_GRAPHS 1    /* 1 (default): a call repeated with identical arguments is
-                                  captured as a CUDA graph on its second occurrence and
-                                  replayed afterwards; 0: plain launches every time */
+#define BBLOCK_OPT_GRAPHS 1    /* 1 (default): a call repeated with identical arguments on a
+                                  created stream (not the legacy or per-thread default
+                                  stream) is captured as a CUDA graph on its second
+                                  occurrence and replayed afterwards; 0: plain launches */
 #define BBLOCK_OPT_TC_NC 2     /* tensor-core forms: complex columns per tile, 16, 32 or 48 */
 #define BBLOCK_OPT_TC_CHUNK 3  /* tensor-core forms: stages between accumulator drains, 1..8 */
 #define BBLOCK_OPT_SLABS 4     /* site slabs per job (split of the site sum), 1..4096 */
@@ -167,6 +168,56 @@ int bblock_profile_enable(bblock_ctx* ctx, int enable);
  * out (one entry per kernel name that launched), set *n_entries, and reset. */
 int bblock_profile_read(bblock_ctx* ctx, bblock_kernel_stat* out, int max_entries,
                         int* n_entries);
+
+/* ---------------------------------------------------------------- tile autotuner
+ * Not in the paper, whose block sizes are tuned by hand for a CPU cache hierarchy
+ * (Sec. 4); here the tile options of a context are chosen by timing candidates on the
+ * caller's own inputs. A learned cost model (a small MLP trained on the GPU by this
+ * library's own kernels) can rank the candidates so that only the top few are timed. */
+
+#define BBLOCK_TUNE_FEATURES 12
+
+typedef struct bblock_costmodel bblock_costmodel;
+
+typedef struct {
+  int nc, chunk, slabs;      /* option values of the candidate (0 = automatic) */
+  float features[BBLOCK_TUNE_FEATURES];  /* cost-model input of the candidate */
+  float predicted;           /* model prediction of log(ms), 0 without a model */
+  double ms;                 /* median time of one compute call, -1 if not timed */
+} bblock_tune_entry;
+
+/* Time the tile candidates of the context's precision on one bblock_compute workload
+ * (same arguments as bblock_compute; B_out is overwritten) and keep the fastest as the
+ * context's options. With a model, all candidates are ranked by predicted time and only
+ * the top_k are timed; without one (model == NULL) every candidate is timed. Each timed
+ * candidate runs once untimed and `repeats` times timed with CUDA events on `stream`.
+ * Up to max_report entries (all candidates, timed or not) go to report; *n_report is set.
+ * Synchronises the stream. */
+int bblock_autotune(bblock_ctx* ctx, int n_t, const void* V, const void* phi1, const void* phi2,
+                    const void* phi3, int nd1, int nd2, int nd3, const int32_t* momenta,
+                    int n_mom, const int32_t* spin_idx, const double* spin_coeffs, int n_spin,
+                    void* B_out, void* stream, bblock_costmodel* model, int top_k, int repeats,
+                    bblock_tune_entry* report, int max_report, int* n_report);
+
+/* Cost model: MLP with two tanh hidden layers of `hidden` units (<= 64), n_features
+ * (<= 16) inputs and one output, deterministic initial weights from `seed`. */
+int bblock_costmodel_create(bblock_costmodel** out, int n_features, int hidden, uint64_t seed,
+                            int device);
+void bblock_costmodel_destroy(bblock_costmodel* model);
+int bblock_costmodel_num_params(const bblock_costmodel* model);
+/* Parameters as FP32, order W1[H][F], b1[H], W2[H][H], b2[H], w3[H], b3 (host buffers). */
+int bblock_costmodel_get_params(bblock_costmodel* model, float* out, int n);
+/* Replace the parameters and reset the optimiser state. */
+int bblock_costmodel_set_params(bblock_costmodel* model, const float* in, int n);
+/* Mean-squared-error loss and its gradient with respect to the parameters over n samples
+ * X [n][F], y [n] (host buffers), computed by the forward and backward kernels on the GPU. */
+int bblock_costmodel_gradient(bblock_costmodel* model, const float* X, const float* y, int n,
+                              float* loss, float* grad);
+/* `epochs` full-batch Adam steps (learning rate lr) on the GPU; *final_loss = last loss. */
+int bblock_costmodel_train(bblock_costmodel* model, const float* X, const float* y, int n,
+                           int epochs, float lr, float* final_loss);
+/* Predictions y [n] for X [n][F] (host buffers). */
+int bblock_costmodel_predict(bblock_costmodel* model, const float* X, int n, float* y);
 
 /* Size of the fixed device scratch used by bblock_contract_noalloc (32 MiB). */
 #define BBLOCK_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)

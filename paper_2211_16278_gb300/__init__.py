@@ -3,7 +3,8 @@
 The compute path is the CUDA library built from ``csrc/`` (C ABI in
 ``include/bblock.h``); :mod:`.bblock` is its Python binding.
 """
-from .bblock import (BblockError, Context, bblock_compute, bblock_compute_batch,  # noqa: F401
+from .bblock import (BblockError, Context, CostModel, bblock_autotune,  # noqa: F401
+                     bblock_compute, bblock_compute_batch,
                      bblock_contract_noalloc,
                      bblock_compute_host, bblock_create, bblock_destroy, bblock_last_error,
                      bblock_last_launch_count, bblock_profile_enable,

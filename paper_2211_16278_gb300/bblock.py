@@ -34,8 +34,12 @@ EXPORTED = (
     "bblock_create", "bblock_destroy", "bblock_last_error", "bblock_status", "bblock_compute",
     "bblock_compute_host", "bblock_compute_batch", "bblock_workspace_bytes",
     "bblock_last_launch_count", "bblock_profile_enable", "bblock_profile_read",
-    "bblock_contract_noalloc", "bblock_set_option", "bblock_get_option",
+    "bblock_contract_noalloc", "bblock_set_option", "bblock_get_option", "bblock_autotune",
+    "bblock_costmodel_create", "bblock_costmodel_destroy", "bblock_costmodel_num_params",
+    "bblock_costmodel_get_params", "bblock_costmodel_set_params", "bblock_costmodel_gradient",
+    "bblock_costmodel_train", "bblock_costmodel_predict",
 )
+TUNE_FEATURES = 12
 OPTIONS = {"graphs": 1, "tc_nc": 2, "tc_chunk": 3, "slabs": 4}
 
 
@@ -60,6 +64,12 @@ class bblock_job(ctypes.Structure):
 class bblock_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int),
                 ("total_ms", ctypes.c_double)]
+
+
+class bblock_tune_entry(ctypes.Structure):
+    _fields_ = [("nc", ctypes.c_int), ("chunk", ctypes.c_int), ("slabs", ctypes.c_int),
+                ("features", ctypes.c_float * TUNE_FEATURES), ("predicted", ctypes.c_float),
+                ("ms", ctypes.c_double)]
 
 
 _lib = None
@@ -105,6 +115,26 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bblock_set_option.restype = I
     lib.bblock_get_option.argtypes = [P, I]
     lib.bblock_get_option.restype = I
+    lib.bblock_autotune.argtypes = [P, I, P, P, P, P, I, I, I, P, I, P, P, I, P, P, P, I, I,
+                                    ctypes.POINTER(bblock_tune_entry), I, ctypes.POINTER(I)]
+    lib.bblock_autotune.restype = I
+    F = ctypes.POINTER(ctypes.c_float)
+    lib.bblock_costmodel_create.argtypes = [ctypes.POINTER(P), I, I, ctypes.c_uint64, I]
+    lib.bblock_costmodel_create.restype = I
+    lib.bblock_costmodel_destroy.argtypes = [P]
+    lib.bblock_costmodel_destroy.restype = None
+    lib.bblock_costmodel_num_params.argtypes = [P]
+    lib.bblock_costmodel_num_params.restype = I
+    lib.bblock_costmodel_get_params.argtypes = [P, F, I]
+    lib.bblock_costmodel_get_params.restype = I
+    lib.bblock_costmodel_set_params.argtypes = [P, F, I]
+    lib.bblock_costmodel_set_params.restype = I
+    lib.bblock_costmodel_gradient.argtypes = [P, F, F, I, F, F]
+    lib.bblock_costmodel_gradient.restype = I
+    lib.bblock_costmodel_train.argtypes = [P, F, F, I, I, ctypes.c_float, F]
+    lib.bblock_costmodel_train.restype = I
+    lib.bblock_costmodel_predict.argtypes = [P, F, I, F]
+    lib.bblock_costmodel_predict.restype = I
     _lib = lib
     return lib
 
@@ -315,3 +345,85 @@ def bblock_contract_noalloc(L: int, q1, q2, q3, momenta, spin_idx, spin_coeffs, 
     if rc != BBLOCK_OK:
         raise BblockError(rc, err.value.decode())
     return B_out
+
+
+# ------------------------------------------------------------------ autotuner and cost model
+
+def _f32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class CostModel:
+    """Owner of a ``bblock_costmodel*`` (MLP trained on the GPU by the library's kernels)."""
+
+    def __init__(self, n_features: int = TUNE_FEATURES, hidden: int = 32, seed: int = 1,
+                 device: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        rc = lib.bblock_costmodel_create(ctypes.byref(h), n_features, hidden, seed, device)
+        if rc != BBLOCK_OK:
+            raise BblockError(rc, "bblock_costmodel_create failed")
+        self.handle, self.F, self.H = h.value, n_features, hidden
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bblock_costmodel_destroy(self.handle)
+            self.handle = None
+
+    def num_params(self) -> int:
+        return int(load().bblock_costmodel_num_params(self.handle))
+
+    def get_params(self) -> np.ndarray:
+        out, ptr = _f32(np.zeros(self.num_params()))
+        _check(None, load().bblock_costmodel_get_params(self.handle, ptr, out.size))
+        return out
+
+    def set_params(self, p) -> None:
+        a, ptr = _f32(p)
+        _check(None, load().bblock_costmodel_set_params(self.handle, ptr, a.size))
+
+    def gradient(self, X, y):
+        Xa, xp = _f32(X)
+        ya, yp = _f32(y)
+        loss, lp = _f32(np.zeros(1))
+        grad, gp = _f32(np.zeros(self.num_params()))
+        _check(None, load().bblock_costmodel_gradient(self.handle, xp, yp, ya.size, lp, gp))
+        return float(loss[0]), grad
+
+    def train(self, X, y, epochs: int = 500, lr: float = 1e-2) -> float:
+        Xa, xp = _f32(X)
+        ya, yp = _f32(y)
+        loss, lp = _f32(np.zeros(1))
+        _check(None, load().bblock_costmodel_train(self.handle, xp, yp, ya.size, epochs, lr, lp))
+        return float(loss[0])
+
+    def predict(self, X) -> np.ndarray:
+        Xa, xp = _f32(X)
+        n = Xa.shape[0]
+        out, op = _f32(np.zeros(n))
+        _check(None, load().bblock_costmodel_predict(self.handle, xp, n, op))
+        return out
+
+
+def bblock_autotune(ctx: Context, V, phi1, phi2, phi3, momenta, spin_idx, spin_coeffs, B_out,
+                    stream=None, model: Optional[CostModel] = None, top_k: int = 3,
+                    repeats: int = 3):
+    """Time tile candidates, keep the fastest in the context; returns one dict per candidate."""
+    n_t = int(V.shape[0])
+    nds = _shape_checks(ctx, V, (phi1, phi2, phi3), n_t)
+    mom, spins, coeffs, per_mom = _spin_arrays(momenta, spin_idx, spin_coeffs)
+    if per_mom:
+        raise ValueError("bblock_autotune takes one coefficient per spin triple")
+    rep = (bblock_tune_entry * 64)()
+    n = ctypes.c_int(0)
+    rc = load().bblock_autotune(
+        ctx.handle, n_t, _dev_ptr(V, "V"), _dev_ptr(phi1, "phi1"), _dev_ptr(phi2, "phi2"),
+        _dev_ptr(phi3, "phi3"), nds[0], nds[1], nds[2], mom.ctypes.data, mom.shape[0],
+        spins.ctypes.data, coeffs.ctypes.data, spins.shape[0], _dev_ptr(B_out, "B_out"),
+        _stream_handle(stream), model.handle if model is not None else None, top_k, repeats,
+        rep, 64, ctypes.byref(n))
+    _check(ctx, rc)
+    return [{"nc": rep[i].nc, "chunk": rep[i].chunk, "slabs": rep[i].slabs,
+             "features": np.array(rep[i].features[:], np.float32),
+             "predicted": float(rep[i].predicted), "ms": float(rep[i].ms)} for i in range(n.value)]

@@ -2,6 +2,8 @@
 // analysis, workspace, phase cache, job tables and the launch sequence
 //   phase table (cached) -> projection (Eq. 2) -> contraction (Eq. 1/3) -> slab reduction.
 #include <algorithm>
+#include <array>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -684,7 +686,9 @@ std::vector<uint64_t> call_signature(const bblock_ctx* c, const std::vector<JobI
 int run_jobs_cached(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momenta,
                     int n_mom, const int32_t* spin_idx, const double* coeffs, int n_spin,
                     int per_mom, cudaStream_t s) {
-  if (!c->opt_graphs || c->prof || jobs.empty() || n_mom == 0)
+  // the legacy and per-thread default streams cannot be captured
+  const bool capturable = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+  if (!c->opt_graphs || c->prof || !capturable || jobs.empty() || n_mom == 0)
     return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
   std::vector<uint64_t> sig = call_signature(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin,
                                              per_mom);
@@ -744,6 +748,78 @@ int run_jobs_cached(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t
   CK(c, cudaGraphLaunch(exec, s));
   c->last_stream = s;
   return BBLOCK_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+
+// How one bblock_compute call with uniform dilution sizes is cut into work units for a
+// given set of tile options (the same rules as run_jobs / run_jobs_tc, one wave).
+struct CallPlan {
+  int nc = 0, chunk = 0, n_slab = 0;
+  long long units = 0;
+  double pad = 0.0;  // padded / actual columns - 1
+};
+
+CallPlan plan_call(const bblock_ctx* c, int n_t, const int nd[3], int n_mom, int pairs,
+                   int nc_opt, int chunk_opt, int slabs_opt) {
+  CallPlan pl;
+  const int X = c->X;
+  if (c->cfg.precision == BBLOCK_FP64) {
+    const int P = std::min(n_mom, kMaxPGroup);
+    const Fp64Tile tl = fp64_tile_for(P);
+    const int xc = fp64_sites_per_chunk(pairs);
+    const int ctas = fp64_contract_ctas_per_sm(P, tl.rn, pairs) * c->num_sms;
+    const long long tiles = (long long)n_t * ((nd[0] * nd[1] + 16 * tl.rm - 1) / (16 * tl.rm)) *
+                            ((nd[2] + 16 * tl.rn - 1) / (16 * tl.rn));
+    int ns = slabs_opt > 0 ? std::min(slabs_opt, (X + xc - 1) / xc) : choose_slabs(tiles, ctas, X, xc, 64);
+    int sps = (X + ns - 1) / ns;
+    sps = (sps + xc - 1) / xc * xc;
+    pl.n_slab = (X + sps - 1) / sps;
+    pl.units = tiles * pl.n_slab;
+    pl.pad = (double)(((nd[2] + 16 * tl.rn - 1) / (16 * tl.rn)) * 16 * tl.rn) / nd[2] - 1.0;
+    return pl;
+  }
+  const int G = tc_groups_per_stage(tc_form_of(c->cfg));
+  pl.chunk = chunk_opt > 0 ? chunk_opt : 2;
+  const long long max_groups_per_unit = 256LL * pl.chunk * G;
+  const int min_slabs = (int)std::min<long long>(X, ((long long)X * pairs + max_groups_per_unit - 1) / max_groups_per_unit);
+  const int max_slabs = std::max(64, min_slabs);
+  std::vector<JobIn> one(1);
+  one[0].nd[0] = nd[0]; one[0].nd[1] = nd[1]; one[0].nd[2] = nd[2];
+  pl.nc = nc_opt > 0 ? nc_opt : choose_nc(one, 0, 1, n_mom);
+  const long long N = (long long)n_mom * nd[2];
+  const long long n_tiles = (N + pl.nc - 1) / pl.nc;
+  const long long tiles = (long long)n_t * ((nd[0] * nd[1] + 127) / 128) * n_tiles;
+  int ns = slabs_opt > 0 ? std::max(min_slabs, std::min(slabs_opt, X))
+                         : std::max(min_slabs, choose_slabs(tiles, c->num_sms, X, 1, max_slabs));
+  const int sps = (X + ns - 1) / ns;
+  pl.n_slab = (X + sps - 1) / sps;
+  pl.units = tiles * pl.n_slab;
+  pl.pad = (double)(n_tiles * pl.nc) / N - 1.0;
+  return pl;
+}
+
+int form_code(const bblock_config& cfg) {
+  if (cfg.precision == BBLOCK_FP64) return 0;
+  if (cfg.precision == BBLOCK_TF32X3) return 4;
+  return cfg.bf16_products == 3 ? 1 : cfg.bf16_products == 9 ? 3 : 2;
+}
+
+void tune_features(const bblock_ctx* c, int n_t, const int nd[3], int n_mom, int pairs,
+                   const CallPlan& pl, float* f) {
+  auto lg = [](double v) { return (float)std::log2(std::max(v, 1.0)); };
+  f[0] = lg((double)nd[0] * nd[1]) / 12.f;
+  f[1] = lg((double)n_mom * nd[2]) / 12.f;
+  f[2] = lg((double)c->X) / 20.f;
+  f[3] = pairs / 16.f;
+  f[4] = pl.nc / 48.f;
+  f[5] = pl.chunk / 4.f;
+  f[6] = lg(pl.n_slab) / 12.f;
+  f[7] = lg((double)pl.units / c->num_sms) / 8.f;
+  f[8] = form_code(c->cfg) / 4.f;
+  f[9] = (float)pl.pad;
+  f[10] = lg(n_t) / 8.f;
+  f[11] = lg(c->cfg.n_ev) / 10.f;
 }
 
 }  // namespace
@@ -928,6 +1004,116 @@ size_t bblock_workspace_bytes(const bblock_ctx* c) {
 }
 
 int bblock_last_launch_count(const bblock_ctx* c) { return c ? c->last_launches : 0; }
+
+int bblock_autotune(bblock_ctx* c, int n_t, const void* V, const void* phi1, const void* phi2,
+                    const void* phi3, int nd1, int nd2, int nd3, const int32_t* momenta,
+                    int n_mom, const int32_t* spin_idx, const double* spin_coeffs, int n_spin,
+                    void* B_out, void* stream, bblock_costmodel* model, int top_k, int repeats,
+                    bblock_tune_entry* report, int max_report, int* n_report) {
+  if (!c) return BBLOCK_ERR_INVALID_ARG;
+  c->err.clear();
+  if (n_report) *n_report = 0;
+  if (n_t < 1 || n_mom < 1 || repeats < 1 || (model && top_k < 1) || (max_report > 0 && !report))
+    return fail(c, BBLOCK_ERR_INVALID_ARG, "bad autotune arguments");
+  int rc = validate_common(c, momenta, n_mom, spin_idx, spin_coeffs, n_spin, 0);
+  if (rc) return rc;
+  SpinPlan sp;
+  rc = plan_spins(c, spin_idx, spin_coeffs, n_spin, 0, n_mom, &sp);
+  if (rc) return rc;
+  const int nd[3] = {nd1, nd2, nd3};
+  // candidate option sets
+  std::vector<std::array<int, 3>> cand;
+  const CallPlan base = plan_call(c, n_t, nd, n_mom, sp.n_pairs, 0, 0, 0);
+  const int a = std::max(1, base.n_slab);
+  const int slab_choices[4] = {0, std::max(1, a / 2), 2 * a, 4 * a};
+  if (c->cfg.precision == BBLOCK_FP64) {
+    for (int k = 0; k < 4; ++k) cand.push_back({0, 0, slab_choices[k]});
+  } else {
+    for (int nc = 16; nc <= 48; nc += 16)
+      for (int ch = 1; ch <= 3; ++ch)
+        for (int k = 0; k < 3; ++k) cand.push_back({nc, ch, slab_choices[k]});
+  }
+  const int n_c = (int)cand.size();
+  std::vector<bblock_tune_entry> ent(n_c);
+  std::vector<float> feat((size_t)n_c * BBLOCK_TUNE_FEATURES);
+  for (int i = 0; i < n_c; ++i) {
+    ent[i].nc = cand[i][0];
+    ent[i].chunk = cand[i][1];
+    ent[i].slabs = cand[i][2];
+    const CallPlan pl = plan_call(c, n_t, nd, n_mom, sp.n_pairs, cand[i][0], cand[i][1], cand[i][2]);
+    tune_features(c, n_t, nd, n_mom, sp.n_pairs, pl, ent[i].features);
+    std::copy(ent[i].features, ent[i].features + BBLOCK_TUNE_FEATURES, feat.begin() + (size_t)i * BBLOCK_TUNE_FEATURES);
+    ent[i].predicted = 0.f;
+    ent[i].ms = -1.0;
+  }
+  std::vector<int> order(n_c);
+  for (int i = 0; i < n_c; ++i) order[i] = i;
+  int n_time = n_c;
+  if (model) {
+    std::vector<float> pred(n_c);
+    rc = bblock_costmodel_predict(model, feat.data(), n_c, pred.data());
+    if (rc) return fail(c, rc, "cost-model prediction failed");
+    for (int i = 0; i < n_c; ++i) ent[i].predicted = pred[i];
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return pred[x] < pred[y]; });
+    n_time = std::min(top_k, n_c);
+  }
+  // time the chosen candidates with plain launches
+  const int saved[4] = {c->opt_graphs, c->opt_tc_nc, c->opt_tc_chunk, c->opt_slabs};
+  const bool saved_prof = c->prof;
+  c->opt_graphs = 0;
+  c->prof = false;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    rc = fail(c, BBLOCK_ERR_CUDA, "cudaEventCreate failed");
+  }
+  int best = -1;
+  for (int r = 0; r < n_time && rc == BBLOCK_OK; ++r) {
+    const int i = order[r];
+    c->opt_tc_nc = cand[i][0];
+    c->opt_tc_chunk = cand[i][1];
+    c->opt_slabs = cand[i][2];
+    std::vector<float> t;
+    for (int k = 0; k <= repeats && rc == BBLOCK_OK; ++k) {
+      if (k > 0) cudaEventRecord(e0, s);
+      rc = bblock_compute(c, n_t, V, phi1, phi2, phi3, nd1, nd2, nd3, momenta, n_mom, spin_idx,
+                          spin_coeffs, n_spin, 0, B_out, stream);
+      if (rc == BBLOCK_OK && k > 0) {
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          cudaGetLastError();
+          rc = fail(c, BBLOCK_ERR_CUDA, "timing failed");
+        }
+        t.push_back(ms);
+      }
+    }
+    if (rc != BBLOCK_OK) break;
+    std::sort(t.begin(), t.end());
+    ent[i].ms = t[t.size() / 2];
+    if (best < 0 || ent[i].ms < ent[best].ms) best = i;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->opt_graphs = saved[0];
+  c->prof = saved_prof;
+  if (rc == BBLOCK_OK && best >= 0) {
+    c->opt_tc_nc = cand[best][0];
+    c->opt_tc_chunk = cand[best][1];
+    c->opt_slabs = cand[best][2];
+  } else {
+    c->opt_tc_nc = saved[1];
+    c->opt_tc_chunk = saved[2];
+    c->opt_slabs = saved[3];
+  }
+  drop_graph(c);
+  c->last_sig.clear();
+  const int n_out = std::min(max_report, n_c);
+  for (int i = 0; i < n_out; ++i) report[i] = ent[i];
+  if (n_report) *n_report = n_out;
+  return rc;
+}
 
 int bblock_set_option(bblock_ctx* c, int option, int value) {
   if (!c) return BBLOCK_ERR_INVALID_ARG;

@@ -43,29 +43,46 @@ def test_graph_replay_is_bitwise_equal_to_plain_launches(env, precision, product
     plain = bb.bblock_create(4, 10, 12, precision, bf16_products=products)
     bb.bblock_set_option(plain, "graphs", 0)
     ref = bb.bblock_compute(plain, V, *phis, inp.momenta, inp.spins, inp.coeffs).cpu().numpy()
-    n_plain = bb.bblock_last_launch_count(plain)
+    first_launches = bb.bblock_last_launch_count(plain)   # includes the phase-table kernel
+    bb.bblock_compute(plain, V, *phis, inp.momenta, inp.spins, inp.coeffs)
+    n_plain = bb.bblock_last_launch_count(plain)           # phase table cached
+    assert first_launches == n_plain + 1
     ctx = bb.bblock_create(4, 10, 12, precision, bf16_products=products)
     assert bb.bblock_get_option(ctx, "graphs") == 1
     B = torch.empty_like(torch.from_numpy(ref)).to("cuda:0")
+    stream = torch.cuda.Stream()       # graphs need a created (capturable) stream
+    torch.cuda.synchronize()
     for call in range(4):          # plain, capture + replay, replay, replay
-        B.zero_()
-        bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B)
+        with torch.cuda.stream(stream):
+            B.zero_()
+        bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B,
+                          stream=stream)
         bb.bblock_status(ctx)
         assert np.array_equal(B.cpu().numpy(), ref), f"call {call}"
-        assert bb.bblock_last_launch_count(ctx) == n_plain
+        assert bb.bblock_last_launch_count(ctx) == (first_launches if call == 0 else n_plain)
     # the inputs change in place: a replay reads them afresh
     phis[0].mul_(2.0)
-    bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B)
+    torch.cuda.synchronize()
+    bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B, stream=stream)
     bb.bblock_status(ctx)
     assert np.allclose(B.cpu().numpy(), 2.0 * ref, rtol=0, atol=1e-12 * np.abs(ref).max())
     # different arguments (another output buffer, other momenta) fall back to plain launches
     B2 = torch.zeros_like(B)
-    bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B2)
+    torch.cuda.synchronize()
+    bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B2, stream=stream)
     mom2 = inp.momenta[:2]
-    B3 = bb.bblock_compute(ctx, V, *phis, mom2, inp.spins, inp.coeffs)
+    B3 = bb.bblock_compute(ctx, V, *phis, mom2, inp.spins, inp.coeffs, stream=stream)
     bb.bblock_status(ctx)
-    assert np.array_equal(B2.cpu().numpy(), B.cpu().numpy())
-    assert np.array_equal(B3.cpu().numpy(), B.cpu().numpy()[:, :2])
+    B_ref2 = B.cpu().numpy()
+    assert np.array_equal(B2.cpu().numpy(), B_ref2)
+    assert np.array_equal(B3.cpu().numpy(), B_ref2[:, :2])
+    # back to the captured arguments: the replay finds the phase table of other momenta
+    # in the context and must restore it first
+    with torch.cuda.stream(stream):
+        B.zero_()
+    bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B, stream=stream)
+    bb.bblock_status(ctx)
+    assert np.array_equal(B.cpu().numpy(), B_ref2)
     bb.bblock_destroy(ctx)
     bb.bblock_destroy(plain)
 
