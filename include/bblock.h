@@ -145,6 +145,9 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 #define BBLOCK_OPT_TC_NC 2     /* tensor-core forms: complex columns per tile, 16, 32 or 48 */
 #define BBLOCK_OPT_TC_CHUNK 3  /* tensor-core forms: stages between accumulator drains, 1..8 */
 #define BBLOCK_OPT_SLABS 4     /* site slabs per job (split of the site sum), 1..4096 */
+#define BBLOCK_OPT_CHECKS 5    /* 1: the tensor-core contraction checks every global index
+                                  against its buffer, skips and records violations (reported
+                                  by bblock_status); 0 (default): no checks */
 
 /* Set an option; BBLOCK_ERR_INVALID_ARG for an unknown option or value. */
 int bblock_set_option(bblock_ctx* ctx, int option, int value);

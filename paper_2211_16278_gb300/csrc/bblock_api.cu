@@ -48,7 +48,8 @@ struct bblock_ctx {
   struct Timed { int kind; cudaEvent_t a, b; };
   std::vector<Timed> timed;
   // options (bblock_set_option)
-  int opt_graphs = 1, opt_tc_nc = 0, opt_tc_chunk = 0, opt_slabs = 0;
+  int opt_graphs = 1, opt_tc_nc = 0, opt_tc_chunk = 0, opt_slabs = 0, opt_checks = 0;
+  unsigned long long* d_dbg = nullptr;  // first index violation of a checked launch
   // CUDA graph of a repeated call: captured on the second call with an identical
   // signature, replayed while the signature and the buffers it points to stay the same
   std::vector<uint64_t> last_sig, graph_sig;
@@ -159,6 +160,41 @@ bool is_device_ptr(const bblock_ctx* c, const void* p) {
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Whether [p, p + bytes) lies inside the device allocation that contains p (driver query
+// cuMemGetAddressRange, reached through the runtime's entry-point lookup; if the query is
+// unavailable the extent is not checked).
+typedef int (*MemRangeFn)(unsigned long long* base, size_t* size, unsigned long long ptr);
+MemRangeFn mem_range_fn() {
+  static MemRangeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<MemRangeFn>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+bool within_allocation(const void* p, size_t bytes) {
+  const MemRangeFn fn = mem_range_fn();
+  if (!fn) return true;
+  unsigned long long base = 0;
+  size_t size = 0;
+  if (fn(&base, &size, reinterpret_cast<unsigned long long>(p)) != 0) return false;
+  return reinterpret_cast<unsigned long long>(p) + bytes <= base + size;
+}
+
+// Whether [p, p + bytes) lies inside the context workspace.
+bool within_workspace(const bblock_ctx* c, const void* p, size_t bytes) {
+  const char* q = static_cast<const char*>(p);
+  return q >= c->d_ws && q + bytes <= c->d_ws + c->ws_cap;
+}
 
 // Spin operator of Eq. (1) reduced to what the kernels consume.
 struct SpinPlan {
@@ -289,7 +325,8 @@ int validate_common(bblock_ctx* c, const int32_t* momenta, int n_mom, const int3
   return BBLOCK_OK;
 }
 
-int validate_job(bblock_ctx* c, const JobIn& j, int idx, bool device) {
+int validate_job(bblock_ctx* c, const JobIn& j, int idx, bool device, int n_mom = 0,
+                 int n_t = 1) {
   const void* ptrs[5] = {j.V, j.phi[0], j.phi[1], j.phi[2], j.B};
   const char* names[5] = {"V", "phi1", "phi2", "phi3", "B_out"};
   for (int k = 0; k < 5; ++k) {
@@ -304,6 +341,16 @@ int validate_job(bblock_ctx* c, const JobIn& j, int idx, bool device) {
     if (j.nd[i] < 1 || j.nd[i] > c->cfg.max_ndil)
       return fail(c, BBLOCK_ERR_INVALID_ARG, "job %d: nd%d = %d outside 1..max_ndil (%d)", idx,
                   i + 1, j.nd[i], c->cfg.max_ndil);
+  if (device) {
+    const size_t sz = sizeof(double2) * (size_t)n_t;
+    const size_t ext[5] = {sz * c->cfg.n_ev * c->rows, sz * 4 * c->cfg.n_ev * j.nd[0],
+                           sz * 4 * c->cfg.n_ev * j.nd[1], sz * 4 * c->cfg.n_ev * j.nd[2],
+                           sz * n_mom * j.nd[0] * j.nd[1] * j.nd[2]};
+    for (int k = 0; k < 5; ++k)
+      if (ext[k] && !within_allocation(ptrs[k], ext[k]))
+        return fail(c, BBLOCK_ERR_INVALID_ARG, "job %d: %s does not hold %zu bytes", idx,
+                    names[k], ext[k]);
+  }
   return BBLOCK_OK;
 }
 
@@ -315,6 +362,7 @@ int tc_form_of(const bblock_config& cfg) {
 // Complex columns per tensor-core tile: the N tile that wastes the fewest padded columns,
 // counting a fixed per-tile cost of 16 columns for building the shared diquark tile.
 int choose_nc(const std::vector<JobIn>& jobs, size_t b, size_t e, int P) {
+  // tiles: 128 (d1, d2) pairs x nc (p, d3) columns
   int best = 48;
   long long best_cost = -1;
   for (int nc = 48; nc >= 16; nc -= 16) {
@@ -424,8 +472,8 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       float2* partial = reinterpret_cast<float2*>(base);
       base += align_up((size_t)n_slab * P_launch * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(float2), 256);
       ws = base;
-      const int m_tiles = (j.nd[0] * j.nd[1] + 127) / 128;
-      const int n_tiles = (P_launch * j.nd[2] + NC - 1) / NC;
+      const int m_tiles = (j.nd[0] * j.nd[1] + 127) / 128;           // (d1, d2) pairs
+      const int n_tiles = (P_launch * j.nd[2] + NC - 1) / NC;        // (p, d3) columns
       for (int set = 0; set < sp.n_coef_sets; ++set) {
         TcJob& tj = tjobs[set][k];
         for (int i = 0; i < 4; ++i) { tj.q1[i] = q1[i]; tj.q2[i] = q2[i]; }
@@ -440,6 +488,15 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       }
       unit += (long long)m_tiles * n_tiles * n_slab;
     }
+    // every field and partial block the kernels will touch lies inside the workspace
+    for (const ProjFieldF& f : fields)
+      if (!within_workspace(c, f.q, (size_t)rows * f.nd * sizeof(float2)))
+        return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: field outside the workspace");
+    for (int k = 0; k < nj; ++k) {
+      const TcJob& tj = tjobs[0][k];
+      if (!within_workspace(c, tj.partial, (size_t)n_slab * P_launch * tj.nd1 * tj.nd2 * tj.nd3 * sizeof(float2)))
+        return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: partial block outside the workspace");
+    }
     const size_t fbytes = align_up(fields.size() * sizeof(ProjFieldF), 256);
     const size_t jbytes = align_up((size_t)nj * sizeof(TcJob), 256);
     std::vector<char> tab(fbytes + jbytes * sp.n_coef_sets);
@@ -450,7 +507,8 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     if (rc) return rc;
     const ProjFieldF* d_fields = reinterpret_cast<const ProjFieldF*>(c->d_tab);
     CK(c, timed_launch(c, K_PROJECT, s, [&] {
-      return launch_project_f32(d_fields, (int)fields.size(), rows, n_ev, max_ndf, s);
+      return launch_project_f32(d_fields, (int)fields.size(), rows, n_ev, max_ndf, c->opt_checks,
+                                c->d_dbg, c->d_status, s);
     }));
     TcParams prm{};
     prm.n_jobs = nj;
@@ -464,6 +522,8 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     prm.NC = NC;
     prm.chunk_stages = chunk_stages;
     prm.status = c->d_status;
+    prm.checks = c->opt_checks;
+    prm.dbg = c->d_dbg;
     const int grid = (int)std::min<long long>(unit, grid_cap);
     for (int set = 0; set < sp.n_coef_sets; ++set) {
       const TcJob* d_jobs = reinterpret_cast<const TcJob*>(c->d_tab + fbytes + jbytes * set);
@@ -471,7 +531,8 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       prm.phase = c->d_phase + (per_mom ? (size_t)set * X : 0);
       CK(c, timed_launch(c, K_CONTRACT, s, [&] { return launch_contract_tc(prm, form, grid, s); }));
       CK(c, timed_launch(c, K_REDUCE, s, [&] {
-        return launch_reduce_slabs_f32(d_jobs, nj, n_slab, P_launch, max_elems, s);
+        return launch_reduce_slabs_f32(d_jobs, nj, n_slab, P_launch, max_elems, c->opt_checks,
+                                       c->d_dbg, c->d_status, s);
       }));
     }
     job_idx = end;
@@ -605,6 +666,14 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       unit += (long long)m_tiles * n_tiles * n_slab;
     }
     // one contiguous table upload: fields, then one job table per coefficient set
+    for (const ProjField& f : fields)
+      if (!within_workspace(c, f.q, (size_t)rows * f.nd * sizeof(double2)))
+        return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: field outside the workspace");
+    for (int k = 0; k < nj; ++k) {
+      const ContractJob& cj = cjobs[0][k];
+      if (!within_workspace(c, cj.partial, (size_t)n_slab * n_mom * cj.nd1 * cj.nd2 * cj.nd3 * sizeof(double2)))
+        return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: partial block outside the workspace");
+    }
     const size_t fbytes = align_up(fields.size() * sizeof(ProjField), 256);
     const size_t jbytes = align_up((size_t)nj * sizeof(ContractJob), 256);
     std::vector<char> tab(fbytes + jbytes * sp.n_coef_sets);
@@ -787,9 +856,9 @@ CallPlan plan_call(const bblock_ctx* c, int n_t, const int nd[3], int n_mom, int
   std::vector<JobIn> one(1);
   one[0].nd[0] = nd[0]; one[0].nd[1] = nd[1]; one[0].nd[2] = nd[2];
   pl.nc = nc_opt > 0 ? nc_opt : choose_nc(one, 0, 1, n_mom);
-  const long long N = (long long)n_mom * nd[2];
+  const long long N = (long long)n_mom * nd[2];                   // (p, d3) columns
   const long long n_tiles = (N + pl.nc - 1) / pl.nc;
-  const long long tiles = (long long)n_t * ((nd[0] * nd[1] + 127) / 128) * n_tiles;
+  const long long tiles = (long long)n_t * (((long long)nd[0] * nd[1] + 127) / 128) * n_tiles;
   int ns = slabs_opt > 0 ? std::max(min_slabs, std::min(slabs_opt, X))
                          : std::max(min_slabs, choose_slabs(tiles, c->num_sms, X, 1, max_slabs));
   const int sps = (X + ns - 1) / ns;
@@ -851,6 +920,8 @@ int bblock_create(bblock_ctx** out, const bblock_config* cfg) {
   if (cudaSetDevice(cfg->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess ||
       cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->d_dbg, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(c->d_dbg, 0, 4 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->tab_free, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     bblock_destroy(c);
@@ -868,6 +939,7 @@ void bblock_destroy(bblock_ctx* c) {
   cudaSetDevice(c->cfg.device);
   cudaDeviceSynchronize();
   cudaFree(c->d_status);
+  cudaFree(c->d_dbg);
   cudaFree(c->d_phase);
   cudaFree(c->d_mom);
   cudaFree(c->d_ws);
@@ -893,7 +965,13 @@ int bblock_status(bblock_ctx* c) {
   int st = 0;
   e = cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "bblock_status readback");
-  if (st) return fail(c, BBLOCK_ERR_DEVICE_FLAG, "device status word 0x%x", st);
+  if (st) {
+    unsigned long long d[4] = {0, 0, 0, 0};
+    if (cudaMemcpy(d, c->d_dbg, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) cudaGetLastError();
+    return fail(c, BBLOCK_ERR_DEVICE_FLAG,
+                "device status word 0x%x (index check: site %llu job %llu index %llu bound %llu)",
+                st, d[0], d[1], d[2], d[3]);
+  }
   return BBLOCK_OK;
 }
 
@@ -923,7 +1001,7 @@ int bblock_compute(bblock_ctx* c, int n_t, const void* V, const void* phi1, cons
     j.nd[0] = nd1; j.nd[1] = nd2; j.nd[2] = nd3;
     j.B = static_cast<double2*>(B_out) + t * bstride;
     if (t == 0) {
-      rc = validate_job(c, j, 0, true);
+      rc = validate_job(c, j, 0, true, n_mom, n_t);
       if (rc) return rc;
     }
   }
@@ -948,7 +1026,7 @@ int bblock_compute_batch(bblock_ctx* c, const bblock_job* jobs_in, int n_jobs,
     j.phi[2] = static_cast<const double2*>(jobs_in[k].phi3);
     j.nd[0] = jobs_in[k].nd1; j.nd[1] = jobs_in[k].nd2; j.nd[2] = jobs_in[k].nd3;
     j.B = static_cast<double2*>(jobs_in[k].B_out);
-    rc = validate_job(c, j, k, true);
+    rc = validate_job(c, j, k, true, n_mom);
     if (rc) return rc;
   }
   // dilution sizes may differ per job: larger jobs first so the persistent grid ends evenly
@@ -1135,6 +1213,12 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       if (value < 0 || value > 4096) break;
       c->opt_slabs = value;
       return BBLOCK_OK;
+    case BBLOCK_OPT_CHECKS:
+      if (value != 0 && value != 1) break;
+      c->opt_checks = value;
+      drop_graph(c);
+      c->last_sig.clear();
+      return BBLOCK_OK;
     default:
       break;
   }
@@ -1148,6 +1232,7 @@ int bblock_get_option(const bblock_ctx* c, int option) {
     case BBLOCK_OPT_TC_NC: return c->opt_tc_nc;
     case BBLOCK_OPT_TC_CHUNK: return c->opt_tc_chunk;
     case BBLOCK_OPT_SLABS: return c->opt_slabs;
+    case BBLOCK_OPT_CHECKS: return c->opt_checks;
     default: return BBLOCK_ERR_INVALID_ARG;
   }
 }

@@ -14,6 +14,7 @@ constexpr int kThreads = 256;   // threads per CTA of the FP64 kernels
 // Device-side status bits (OR-ed into the context's status word).
 constexpr int kStatusBadJob = 1;
 constexpr int kStatusTimeout = 2;   // a bounded wait of the tensor-core kernel gave up
+constexpr int kStatusBadIndex = 4;  // a checked kernel found an index outside its buffer
 
 // One reconstructed field of Eq. (2):
 //   q[r][d] = sum_l V[l][r] * Phi[l][d],   Phi[l][d] = sum_t w[t] * phi[row_off[t] + l][d],
@@ -104,16 +105,22 @@ struct TcParams {
   int NC;                        // complex columns per tile: 16, 32 or 48
   int chunk_stages;              // stages accumulated in TMEM between drains
   int* status;
+  // index checks (debug option): every global access is checked against its buffer; the
+  // first violation is recorded in dbg[0..3] = (site code, job, index, bound) and skipped
+  int checks;
+  unsigned long long* dbg;
 };
 
 enum TcForm { TC_BF16_3 = 0, TC_BF16_6 = 1, TC_BF16_9 = 2, TC_TF32_3 = 3 };
 
 cudaError_t launch_project_f32(const ProjFieldF* d_fields, int n_fields, int rows, int n_ev,
-                               int max_nd, cudaStream_t s);
+                               int max_nd, int checks, unsigned long long* dbg, int* status,
+                               cudaStream_t s);
 cudaError_t launch_contract_tc(const TcParams& p, int form, int grid, cudaStream_t s);
 int tc_groups_per_stage(int form);
 cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab, int P_total,
-                                    long long max_elems, cudaStream_t s);
+                                    long long max_elems, int checks, unsigned long long* dbg,
+                                    int* status, cudaStream_t s);
 
 cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, cudaStream_t s);
 cudaError_t launch_project_fp64(const ProjField* d_fields, int n_fields, int rows, int n_ev,

@@ -11,8 +11,21 @@ namespace bb {
 
 constexpr int FBM = 128, FBN = 32, FBK = 16;
 
+__device__ __forceinline__ bool f32_idx_ok(long long i, long long n, int code, int field,
+                                           unsigned long long* dbg, int* status) {
+  if (i >= 0 && i < n) return true;
+  if (atomicCAS(dbg, 0ull, (unsigned long long)code) == 0ull) {
+    dbg[1] = (unsigned long long)field;
+    dbg[2] = (unsigned long long)i;
+    dbg[3] = (unsigned long long)n;
+  }
+  atomicOr(status, kStatusBadIndex);
+  return false;
+}
+
 __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __restrict__ fields,
-                                                          int rows, int n_ev) {
+                                                          int rows, int n_ev, int checks,
+                                                          unsigned long long* dbg, int* status) {
   __shared__ float2 As[FBK][FBM];
   __shared__ float2 Bs[FBK][FBN];
   const ProjFieldF& F = fields[blockIdx.x];
@@ -37,7 +50,8 @@ __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __re
       const int r = idx % FBM, kk = idx / FBM;
       const int l = kb + kk, row = m0 + r;
       float2 v = make_float2(0.f, 0.f);
-      if (l < n_ev && row < rows) {
+      if (l < n_ev && row < rows &&
+          (!checks || f32_idx_ok((long long)l * rows + row, (long long)n_ev * rows, 11, blockIdx.x, dbg, status))) {
         const double2 d = F.V[(size_t)l * rows + row];
         v = make_float2((float)d.x, (float)d.y);
       }
@@ -49,6 +63,9 @@ __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __re
       float2 b = make_float2(0.f, 0.f);
       if (l < n_ev && col < nd) {
         for (int t = 0; t < n_terms; ++t) {
+          if (checks && !f32_idx_ok((long long)(F.row_off[t] + l) * nd + col, 4LL * n_ev * nd, 12,
+                                    blockIdx.x, dbg, status))
+            continue;
           const double2 d = F.phi[(size_t)(F.row_off[t] + l) * nd + col];
           const float2 f = make_float2((float)d.x, (float)d.y);
           b.x = fmaf(wt[t].x, f.x, fmaf(-wt[t].y, f.y, b.x));
@@ -82,16 +99,19 @@ __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __re
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int col = n0 + tn + 8 * j;
-      if (col < nd) F.q[(size_t)row * nd + col] = acc[i][j];
+      if (col < nd && (!checks || f32_idx_ok((long long)row * nd + col, (long long)rows * nd, 13,
+                                              blockIdx.x, dbg, status)))
+        F.q[(size_t)row * nd + col] = acc[i][j];
     }
   }
 }
 
 cudaError_t launch_project_f32(const ProjFieldF* d_fields, int n_fields, int rows, int n_ev,
-                               int max_nd, cudaStream_t s) {
+                               int max_nd, int checks, unsigned long long* dbg, int* status,
+                               cudaStream_t s) {
   if (n_fields == 0 || rows == 0) return cudaSuccess;
   dim3 grid(n_fields, (rows + FBM - 1) / FBM, (max_nd + FBN - 1) / FBN);
-  k_project_f32<<<grid, kThreads, 0, s>>>(d_fields, rows, n_ev);
+  k_project_f32<<<grid, kThreads, 0, s>>>(d_fields, rows, n_ev, checks, dbg, status);
   return cudaGetLastError();
 }
 

@@ -212,6 +212,20 @@ struct Unit {
   int job, mt, nt, slab, x_begin, x_end, n_stages;
 };
 
+// Index check of the debug option: false (and the first violation recorded) if i is
+// outside [0, n).
+__device__ __forceinline__ bool idx_ok(const TcParams& prm, long long i, long long n, int code,
+                                       int job) {
+  if (i >= 0 && i < n) return true;
+  if (atomicCAS(prm.dbg, 0ull, (unsigned long long)code) == 0ull) {
+    prm.dbg[1] = (unsigned long long)job;
+    prm.dbg[2] = (unsigned long long)i;
+    prm.dbg[3] = (unsigned long long)n;
+  }
+  atomicOr(prm.status, kStatusBadIndex);
+  return false;
+}
+
 __device__ __forceinline__ Unit decode_unit(const TcParams& prm, long long u, int G) {
   Unit w;
   w.job = tc_find_job(prm.jobs, prm.n_jobs, u);
@@ -243,7 +257,7 @@ __device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t parity,
   }
 }
 
-template <bool TF32, int LEVELS, int NPROD>
+template <bool TF32, int LEVELS, int NPROD, bool CHECKS>
 __global__ void __launch_bounds__(Roles<TF32>::kThreads, 1)
 k_contract_tc(const __grid_constant__ TcParams prm) {
   using R = Roles<TF32>;
@@ -305,8 +319,9 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
 
   if (warp >= kProdWarp0) {
     // ------------------------------------------------------------ producers
-    // Thread roles are fixed: pt < kAThreads builds diquark rows, the rest build third-quark
-    // rows; each thread owns one row and 8 consecutive groups (half h) of every stage.
+    // Thread roles are fixed: pt < kAThreads builds diquark rows (M side), the rest build
+    // phase x third-quark rows (N side); each thread owns one row and 8 consecutive groups
+    // (half h) of every stage.
     const int pt = tid - kProdWarp0 * 32;
     const bool is_a = pt < R::kAThreads;
     const int rr = is_a ? pt % kTcM : (pt - R::kAThreads) % kMaxNC;
@@ -321,11 +336,13 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
       bool row_ok;
       int off1 = 0, off2 = 0, s1 = 0, s2 = 0, pidx = 0;
       if (is_a) {
+        // M side: diquark of the pair m = d1 * nd2 + d2
         const int m = w.mt * kTcM + rr;
         row_ok = m < nd1 * nd2;
         const int d1 = row_ok ? m / nd2 : 0, d2 = row_ok ? m - d1 * nd2 : 0;
         off1 = d1; off2 = d2; s1 = nd1; s2 = nd2;
       } else {
+        // N side: phase x third quark of the column n = p * nd3 + d3
         const int n = w.nt * NC + rr;
         row_ok = row_used && n < prm.P * nd3;
         const int p = row_ok ? n / nd3 : 0, d3 = row_ok ? n - p * nd3 : 0;
@@ -338,6 +355,8 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
         s_q2[pt] = J.q2[prm.b_slot[pt]];
         s_q3[pt] = J.q3[pt];
       }
+      // bar.sync is warp-aligned: reconverge every warp before it
+      __syncwarp();
       named_bar(kBarProd, R::kProdThreads);
       const double2* phase_p = prm.phase + (size_t)pidx * prm.X;
       for (int st = 0; st < w.n_stages; ++st, ++s_g) {
@@ -360,7 +379,15 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
             for (int j = 0; j < 4; ++j) {
               const int x = w.x_begin + xl;
               vld[j] = row_ok && x < w.x_end;
-              const int xs = vld[j] ? x : w.x_begin;
+              int xs = vld[j] ? x : w.x_begin;
+              if (CHECKS) {
+                const long long fl = 3LL * prm.X * s1;            // elements of a field
+                bool good = idx_ok(prm, (long long)xs * 3 * s1 + off1 + 2LL * s1, fl, is_a ? 1 : 3, w.job) &&
+                            idx_ok(prm, pr, np, 6, w.job);
+                if (is_a) good = good && idx_ok(prm, (long long)xs * 3 * s2 + off2 + 2LL * s2, 3LL * prm.X * s2, 2, w.job);
+                else good = good && idx_ok(prm, (long long)pidx * prm.X + xs, (long long)prm.P * prm.X, 4, w.job);
+                if (!good) { vld[j] = false; xs = 0; pr = 0; }
+              }
               if (is_a) {
                 const float2* uq = s_q1[pr] + (size_t)xs * 3 * s1 + off1;
                 const float2* vq = s_q2[pr] + (size_t)xs * 3 * s2 + off2;
@@ -414,8 +441,10 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
           }
         }
         fence_async_smem();
+        __syncwarp();
         named_bar(kBarProd, R::kProdThreads);
         if (pt == 0) mbar_arrive(smem_u32(&bar_full[slot]));
+        __syncwarp();
       }
     }
   } else if (warp == kMmaWarp) {
@@ -510,14 +539,17 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
           tmem_wait_st();
         }
         tc_fence_before();
+        __syncwarp();
         named_bar(kBarEpi, kEpiWarps * 32);
         if (tid == 0) mbar_arrive(smem_u32(&bar_acc_empty[buf]));
+        __syncwarp();   // tcgen05.ld below is warp-aligned
         if (ok && ch == n_chunks - 1) {
           // unit done: write the FP32 running sum as this slab's partial block
           const int m = w.mt * kTcM + row;
           const int M = J.nd1 * J.nd2, nd3 = J.nd3, Ntot = prm.P * nd3;
           for (int col = 0; col < NC; col += 16) {
             float vr[16], vi[16];
+            __syncwarp();   // the stores below may diverge; tcgen05.ld is warp-aligned
             tmem_ld16(run_r + col, vr);
             tmem_ld16(run_r + NC + col, vi);
             tmem_wait_ld();
@@ -527,8 +559,9 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
                 const int n = w.nt * NC + col + i;
                 if (n < Ntot) {
                   const int p = n / nd3, d3 = n - p * nd3;
-                  J.partial[(((size_t)w.slab * prm.P + p) * M + m) * nd3 + d3] =
-                      make_float2(vr[i], vi[i]);
+                  const size_t pi = (((size_t)w.slab * prm.P + p) * M + m) * nd3 + d3;
+                  if (!CHECKS || idx_ok(prm, (long long)pi, (long long)prm.n_slab * prm.P * M * nd3, 5, w.job))
+                    J.partial[pi] = make_float2(vr[i], vi[i]);
                 }
               }
             }
@@ -540,6 +573,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
 
   // ------------------------------------------------------------ teardown
   tc_fence_before();
+  __syncwarp();
   __syncthreads();
   if (warp == kMmaWarp) {
     tc_fence_after();
@@ -548,18 +582,25 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
   }
 }
 
-template <bool TF32, int LEVELS, int NPROD>
-cudaError_t launch_form(const TcParams& prm, int grid, cudaStream_t s) {
+template <bool TF32, int LEVELS, int NPROD, bool CHECKS>
+cudaError_t launch_variant(const TcParams& prm, int grid, cudaStream_t s) {
   constexpr int STAGES = LEVELS == 3 ? 2 : 3;
   const size_t smem = (size_t)STAGES * LEVELS * 2 * (kAPlaneBytes + kBPlaneBytes);
-  cudaError_t e = cudaFuncSetAttribute(k_contract_tc<TF32, LEVELS, NPROD>,
+  cudaError_t e = cudaFuncSetAttribute(k_contract_tc<TF32, LEVELS, NPROD, CHECKS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_contract_tc<TF32, LEVELS, NPROD><<<grid, Roles<TF32>::kThreads, smem, s>>>(prm);
+  k_contract_tc<TF32, LEVELS, NPROD, CHECKS><<<grid, Roles<TF32>::kThreads, smem, s>>>(prm);
   return cudaGetLastError();
 }
 
-__global__ void k_reduce_slabs_f32(const TcJob* __restrict__ jobs, int n_slab, int P_total) {
+template <bool TF32, int LEVELS, int NPROD>
+cudaError_t launch_form(const TcParams& prm, int grid, cudaStream_t s) {
+  return prm.checks ? launch_variant<TF32, LEVELS, NPROD, true>(prm, grid, s)
+                    : launch_variant<TF32, LEVELS, NPROD, false>(prm, grid, s);
+}
+
+__global__ void k_reduce_slabs_f32(const TcJob* __restrict__ jobs, int n_slab, int P_total,
+                                   int checks, unsigned long long* dbg, int* status) {
   const TcJob& J = jobs[blockIdx.y];
   const long long per = (long long)P_total * J.nd1 * J.nd2 * J.nd3;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per;
@@ -572,6 +613,7 @@ __global__ void k_reduce_slabs_f32(const TcJob* __restrict__ jobs, int n_slab, i
     }
     J.B[e] = make_double2(sr, si);
   }
+  (void)checks; (void)dbg; (void)status;  // every index above is below n_slab * per or per
 }
 
 }  // namespace
@@ -592,12 +634,13 @@ cudaError_t launch_contract_tc(const TcParams& prm, int form, int grid, cudaStre
 }
 
 cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab, int P_total,
-                                    long long max_elems, cudaStream_t s) {
+                                    long long max_elems, int checks, unsigned long long* dbg,
+                                    int* status, cudaStream_t s) {
   if (n_jobs == 0 || max_elems == 0) return cudaSuccess;
   long long bx = (max_elems + kThreads - 1) / kThreads;
   if (bx > 4096) bx = 4096;
   dim3 grid((unsigned)bx, n_jobs);
-  k_reduce_slabs_f32<<<grid, kThreads, 0, s>>>(d_jobs, n_slab, P_total);
+  k_reduce_slabs_f32<<<grid, kThreads, 0, s>>>(d_jobs, n_slab, P_total, checks, dbg, status);
   return cudaGetLastError();
 }
 
