@@ -148,6 +148,10 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 #define BBLOCK_OPT_CHECKS 5    /* 1: the tensor-core contraction checks every global index
                                   against its buffer, skips and records violations (reported
                                   by bblock_status); 0 (default): no checks */
+#define BBLOCK_OPT_WAVE_MB 6   /* workspace budget of one wave of jobs, MiB: a batch whose
+                                  fields and partial blocks exceed it runs as several waves
+                                  of launches; 0 (default): half the device memory free at
+                                  bblock_create, at most 96 GiB */
 
 /* Set an option; BBLOCK_ERR_INVALID_ARG for an unknown option or value. */
 int bblock_set_option(bblock_ctx* ctx, int option, int value);

@@ -56,9 +56,13 @@ struct bblock_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   int graph_launches = 0;
   bool capturing = false;
+  // pinned staging that a captured graph's table copies read at every replay: each upload
+  // of the captured call (one per wave) keeps its own slot, at graph_tab_off onwards
   char* h_graph_tab = nullptr;
   size_t h_graph_tab_cap = 0;
-  size_t last_tab_bytes = 0;
+  size_t graph_tab_off = 0;
+  size_t call_tab_bytes = 0;  // slots the last call's uploads took, summed over its waves
+  size_t opt_wave_bytes = 0;  // workspace budget per wave set by the caller (0: default)
 };
 
 namespace {
@@ -121,6 +125,10 @@ int cuda_fail(bblock_ctx* c, cudaError_t e, const char* what) {
   } while (0)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Workspace one wave of jobs may take: the caller's limit, else half the free memory seen at
+// creation (at most 96 GiB). A job larger than the budget still runs, alone in its wave.
+size_t wave_budget(const bblock_ctx* c) { return c->opt_wave_bytes ? c->opt_wave_bytes : c->ws_budget; }
 
 void drop_graph(bblock_ctx* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -262,15 +270,19 @@ int ensure_phase(bblock_ctx* c, const int32_t* momenta, int n_mom, cudaStream_t 
   return BBLOCK_OK;
 }
 
-// Copy `bytes` of host tables into the device table buffer on `s` via the pinned staging buffer.
+// Copy `bytes` of host tables into the device table buffer on `s` via pinned staging.
 int upload_tables(bblock_ctx* c, const void* src, size_t bytes, cudaStream_t s) {
-  c->last_tab_bytes = bytes;
+  const size_t slot = align_up(bytes, 256);
+  c->call_tab_bytes += slot;
   if (c->capturing) {
-    // the graph's memcpy node reads this buffer at every replay; it is sized beforehand
-    if (bytes > c->h_graph_tab_cap || bytes > c->tab_cap)
+    // The graph's memcpy node reads its slot at every replay, so every wave of the captured
+    // call needs a slot of its own: a shared one would hand every wave the last wave's tables.
+    if (c->graph_tab_off + bytes > c->h_graph_tab_cap || bytes > c->tab_cap)
       return fail(c, BBLOCK_ERR_UNSUPPORTED, "table growth during graph capture");
-    memcpy(c->h_graph_tab, src, bytes);
-    CK(c, cudaMemcpyAsync(c->d_tab, c->h_graph_tab, bytes, cudaMemcpyHostToDevice, s));
+    char* h = c->h_graph_tab + c->graph_tab_off;
+    memcpy(h, src, bytes);
+    CK(c, cudaMemcpyAsync(c->d_tab, h, bytes, cudaMemcpyHostToDevice, s));
+    c->graph_tab_off += slot;
     return BBLOCK_OK;
   }
   if (c->tab_free) CK(c, cudaEventSynchronize(c->tab_free));  // previous upload has drained
@@ -404,7 +416,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     size_t end = job_idx, need = 0;
     while (end < jobs.size()) {
       size_t b = job_bytes(jobs[end], max_slabs);
-      if (end > job_idx && need + b > c->ws_budget) break;
+      if (end > job_idx && need + b > wave_budget(c)) break;
       need += b;
       ++end;
     }
@@ -546,6 +558,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
              cudaStream_t s) {
   c->last_launches = 0;
   c->last_stream = s;
+  c->call_tab_bytes = 0;
   if (jobs.empty() || n_mom == 0) return BBLOCK_OK;
   CK(c, cudaSetDevice(c->cfg.device));
   SpinPlan sp;
@@ -577,7 +590,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
     size_t end = job_idx, need = 0;
     while (end < jobs.size()) {
       size_t b = job_bytes(jobs[end], max_slabs);
-      if (end > job_idx && need + b > c->ws_budget) break;
+      if (end > job_idx && need + b > wave_budget(c)) break;
       need += b;
       ++end;
     }
@@ -733,6 +746,7 @@ std::vector<uint64_t> call_signature(const bblock_ctx* c, const std::vector<JobI
               ((uint64_t)per_mom << 16) | ((uint64_t)c->opt_tc_nc << 24) |
               ((uint64_t)c->opt_tc_chunk << 32) | ((uint64_t)c->opt_slabs << 40));
   k.push_back((uint64_t)n_mom | ((uint64_t)n_spin << 32));
+  k.push_back((uint64_t)wave_budget(c));
   for (int i = 0; i < 3 * n_mom; ++i) k.push_back((uint64_t)(uint32_t)momenta[i]);
   for (int i = 0; i < 3 * n_spin; ++i) k.push_back((uint64_t)(uint32_t)spin_idx[i]);
   const int n_coef = 2 * n_spin * (per_mom ? n_mom : 1);
@@ -777,19 +791,24 @@ int run_jobs_cached(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t
   }
   // second identical call: every buffer already has its size, so capture it
   drop_graph(c);
-  if (c->h_graph_tab_cap < c->last_tab_bytes) {
-    if (c->h_graph_tab) cudaFreeHost(c->h_graph_tab);
+  if (c->h_graph_tab_cap < c->call_tab_bytes) {
+    if (c->h_graph_tab) {
+      // an older graph that read this staging has been dropped, but a replay may be in flight
+      if (c->last_stream) CK(c, cudaStreamSynchronize(c->last_stream));
+      cudaFreeHost(c->h_graph_tab);
+    }
     c->h_graph_tab = nullptr;
     c->h_graph_tab_cap = 0;
-    if (cudaHostAlloc(&c->h_graph_tab, c->last_tab_bytes, cudaHostAllocDefault) != cudaSuccess) {
+    if (cudaHostAlloc(&c->h_graph_tab, c->call_tab_bytes, cudaHostAllocDefault) != cudaSuccess) {
       cudaGetLastError();
       return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
     }
-    c->h_graph_tab_cap = c->last_tab_bytes;
+    c->h_graph_tab_cap = c->call_tab_bytes;
   }
   CK(c, cudaSetDevice(c->cfg.device));
   // the previous plain upload must have drained before the capture reuses the device tables
   if (c->tab_free) CK(c, cudaEventSynchronize(c->tab_free));
+  c->graph_tab_off = 0;
   CK(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   c->capturing = true;
   int rc = run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
@@ -1219,6 +1238,10 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       drop_graph(c);
       c->last_sig.clear();
       return BBLOCK_OK;
+    case BBLOCK_OPT_WAVE_MB:
+      if (value < 0) break;
+      c->opt_wave_bytes = (size_t)value << 20;
+      return BBLOCK_OK;
     default:
       break;
   }
@@ -1232,6 +1255,7 @@ int bblock_get_option(const bblock_ctx* c, int option) {
     case BBLOCK_OPT_TC_NC: return c->opt_tc_nc;
     case BBLOCK_OPT_TC_CHUNK: return c->opt_tc_chunk;
     case BBLOCK_OPT_SLABS: return c->opt_slabs;
+    case BBLOCK_OPT_WAVE_MB: return (int)(c->opt_wave_bytes >> 20);
     case BBLOCK_OPT_CHECKS: return c->opt_checks;
     default: return BBLOCK_ERR_INVALID_ARG;
   }

@@ -118,3 +118,58 @@ def test_bad_option_values_are_rejected(env):
         with pytest.raises(bb.BblockError, match="INVALID_ARG"):
             bb.bblock_set_option(ctx, opt, val)
     bb.bblock_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision,products,tol", [("fp64", 6, 1e-12), ("bf16", 6, 1e-6),
+                                                    ("tf32x3", 6, 1e-6)])
+def test_multi_wave_batch_graph_replay(env, precision, products, tol):
+    """A batch that runs as several waves of launches (a small workspace budget per wave),
+    with mixed dilution sizes, captured and replayed: each wave's table copy in the graph
+    must carry that wave's jobs."""
+    torch, bb = env
+    L, n_ev, mom = 6, 16, [(0, 0, 0), (1, 0, 0), (1, 1, 0)]
+    spins, coeffs = [(0, 1, 0), (1, 0, 0), (2, 3, 2)], [0.7, -0.7, 0.7]
+    dev = torch.device("cuda:0")
+    inps = [workloads.custom(L, n_ev, nd, 3, mom, spins, coeffs, seed=3200 + k)
+            for k, nd in enumerate([(16, 16, 16), (12, 12, 16), (16, 12, 8)])]
+    jobs_dev, outs = [], []
+    for inp in inps:
+        V = torch.from_numpy(inp.V).to(dev)
+        phis = [torch.from_numpy(inp.phi[0][i]).to(dev) for i in range(3)]
+        Bk = torch.zeros((inp.workload.n_t, len(mom), *inp.ndil[0]), dtype=torch.complex128, device=dev)
+        outs.append(Bk)
+        for t in range(inp.workload.n_t):
+            jobs_dev.append((V[t], phis[0][t], phis[1][t], phis[2][t], Bk[t]))
+    stream = torch.cuda.Stream()
+
+    def run(ctx):
+        with torch.cuda.stream(stream):
+            for Bk in outs:
+                Bk.zero_()
+        bb.bblock_compute_batch(ctx, jobs_dev, mom, spins, coeffs, stream=stream)
+        bb.bblock_status(ctx)
+        stream.synchronize()
+        return [Bk.cpu().numpy() for Bk in outs], bb.bblock_last_launch_count(ctx)
+
+    one_wave = bb.bblock_create(L, n_ev, 16, precision, bf16_products=products)
+    bb.bblock_set_option(one_wave, "graphs", 0)
+    _, n_one = run(one_wave)
+    plain = bb.bblock_create(L, n_ev, 16, precision, bf16_products=products)
+    bb.bblock_set_option(plain, "graphs", 0)
+    bb.bblock_set_option(plain, "wave_mb", 16)
+    assert bb.bblock_get_option(plain, "wave_mb") == 16
+    ref, n_plain = run(plain)
+    assert n_plain - 1 >= 3 * (n_one - 1)     # at least 3 waves (the first launch: phase table)
+    for k, inp in enumerate(inps):
+        for t in (0, inp.workload.n_t - 1):
+            want = oracle.bblock(L, inp.V[t], *[inp.phi[0][i][t] for i in range(3)], mom, spins, coeffs)
+            assert rel(ref[k][t], want) <= tol, (k, t)
+    ctx = bb.bblock_create(L, n_ev, 16, precision, bf16_products=products)
+    bb.bblock_set_option(ctx, "wave_mb", 16)
+    for call in range(4):          # plain, capture + replay, replay, replay
+        got, n = run(ctx)
+        for k in range(len(inps)):
+            assert np.array_equal(got[k], ref[k]), (call, k)
+        assert n == (n_plain if call == 0 else n_plain - 1)   # phase table cached after call 0
+    for c in (one_wave, plain, ctx):
+        bb.bblock_destroy(c)
