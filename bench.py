@@ -1,13 +1,18 @@
 #!/usr/bin/env python
-"""Baryon-block throughput on GB300: blocks/s of the L=24, N_ev=96, N_dil=32 workload.
+"""Baryon-block throughput on GB300 (blocks/s), by default for the L=24, N_ev=96, N_dil=32
+workload in the FP64 form.
 
 One step = the whole hot path (phase table from cache, projection of the three quark
-lines for every spin used, fused diquark + contraction, slab reduction) over 8 time
-slices x 3 momenta x one 3-triple baryon operator, i.e. 24 blocks B[t][p][d1][d2][d3].
-Inputs are seeded synthetic draws (``workloads.py``) resident on the device.
+lines for every spin used, fused diquark + contraction, slab reduction) over every block
+of the workload; for the default workload 8 time slices x 3 momenta x one 3-triple baryon
+operator, i.e. 24 blocks B[t][p][d1][d2][d3]. Inputs are seeded synthetic draws
+(``workloads.py``) resident on the device.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload NAME] [--form fp64|bf16x6|bf16x9|tf32x3|bf16x3]
 
+``--workload`` selects another named workload (the batched one, with six noise triples of
+uneven dilution size, runs as one batched call per step and defaults to the bf16x6 form).
 Prints one JSON line (rank 0). Under torchrun every rank computes its own independent
 time slices (weak scaling, no data-path collective); the timed region is bracketed by a
 barrier and the maximum over ranks is reported.
@@ -71,6 +76,9 @@ def parse_args():
                     help="target CPU seconds of one oracle sample")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the tensor-core forms (time the FP64 form only)")
+    ap.add_argument("--form", choices=["fp64", "bf16x6", "bf16x9", "tf32x3", "bf16x3"],
+                    default=None, help="form of the headline number (default: fp64; bf16x6 "
+                    "for the batched workload)")
     ap.add_argument("--n-t", type=int, default=None,
                     help="time slices per step (default: the workload's); for profiling runs")
     return ap.parse_args()
@@ -240,6 +248,35 @@ def load_traffic(kernel: str):
     return None
 
 
+def rank_inputs(w, rank: int):
+    """Inputs of one rank: every rank draws its own time slices (its own seed), so the
+    ranks share no work and exchange no data."""
+    return workloads.generate(w, seed=w.seed + rank)
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (the timing that is reported)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, blocks_per_step: int, steps: int, seconds: float) -> float:
+    """Whole-job blocks/s: the blocks of all ranks over the slowest rank's time."""
+    return world * blocks_per_step * steps / seconds
+
+
+FORMS = {  # name: (precision, bf16 products, MMA piece products, tensor peak TFLOP/s)
+    "fp64": ("fp64", 6, 0, None),
+    "bf16x6": ("bf16", 6, 6, BF16_PEAK_TFLOPS), "bf16x9": ("bf16", 9, 9, BF16_PEAK_TFLOPS),
+    "tf32x3": ("tf32x3", 6, 3, TF32_PEAK_TFLOPS), "bf16x3": ("bf16", 3, 3, BF16_PEAK_TFLOPS),
+}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -262,26 +299,46 @@ def run_ours(args):
     if args.n_t is not None:
         import dataclasses
         w = dataclasses.replace(w, n_t=args.n_t)
-    inp = workloads.generate(w, seed=w.seed + rank)  # each rank: its own time slices
-    nd = inp.ndil[0]
+    batched = w.n_noise > 1
+    head = args.form or ("bf16x6" if batched else "fp64")
+    inp = rank_inputs(w, rank)
     P = len(inp.momenta)
     n_alpha, n_beta, pairs = spin_structure(inp.spins)
+    max_nd = max(max(nd) for nd in inp.ndil)
     V = torch.from_numpy(inp.V).to(dev)
-    phis = [torch.from_numpy(inp.phi[0][i]).to(dev) for i in range(3)]
+    phis = [[torch.from_numpy(inp.phi[k][i]).to(dev) for i in range(3)] for k in range(w.n_noise)]
+    # jobs: (noise triple, time slice); a single-noise workload is one call over all slices
+    job_nd = [inp.ndil[k] for k in range(w.n_noise) for _ in range(w.n_t)]
     # a created stream: repeated calls are then replayed from a CUDA graph by the library
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize(dev)
-    blocks_per_step = w.n_t * P
+    blocks_per_step = len(job_nd) * P
+    contract_alg = sum(contraction_flops(w.X, nd, P, pairs) for nd in job_nd)
+    project_alg = sum(projection_flops(w.X, w.n_ev, nd, n_alpha, n_beta, pairs) for nd in job_nd)
+    # useful complex GEMM work of the folded contraction: 8 M N K per job, K = 3 pairs X
+    gemm_flops = sum(8.0 * nd[0] * nd[1] * (P * nd[2]) * (3 * pairs * w.X) for nd in job_nd)
 
-    def measure(precision, products, sampler=None):
+    def outputs():
+        return [torch.empty((w.n_t, P, *inp.ndil[k]), dtype=torch.complex128, device=dev)
+                for k in range(w.n_noise)]
+
+    def measure(form, sampler=None):
         """W untimed + K timed steps of one form; CUDA events on the launching stream."""
-        c = bb.bblock_create(w.L, w.n_ev, max(nd), precision, bf16_products=products,
+        precision, products = FORMS[form][:2]
+        c = bb.bblock_create(w.L, w.n_ev, max_nd, precision, bf16_products=products,
                              device=local)
-        out = torch.empty((w.n_t, P, *nd), dtype=torch.complex128, device=dev)
+        outs = outputs()
+        if batched:
+            jobs = [(V[t], phis[k][0][t], phis[k][1][t], phis[k][2][t], outs[k][t])
+                    for k in range(w.n_noise) for t in range(w.n_t)]
 
-        def step():
-            bb.bblock_compute(c, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=out,
-                              stream=stream)
+            def step():
+                bb.bblock_compute_batch(c, jobs, inp.momenta, inp.spins, inp.coeffs,
+                                        stream=stream)
+        else:
+            def step():
+                bb.bblock_compute(c, V, *phis[0], inp.momenta, inp.spins, inp.coeffs,
+                                  B_out=outs[0], stream=stream)
 
         for _ in range(args.warmup):
             step()
@@ -310,82 +367,109 @@ def run_ours(args):
         t_ms = e0.elapsed_time(e1)
         prof = bb.bblock_profile_read(c)
         bb.bblock_profile_enable(c, False)
-        if world > 1:
-            t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_ms = float(t.item())
-        return c, out, t_ms, prof, n_launch
+        t_ms = max_over_ranks(t_ms, world, dev)
+        return c, outs, t_ms, prof, n_launch
+
+    def tensor_roofline(form, prof):
+        nprod, peak = FORMS[form][2:]
+        nc, msc = prof.get("contract", (0, 0.0))
+        # executed MMA flops of the timed steps / the contraction launches' summed time
+        execd = gemm_flops * nprod * args.steps / (msc / 1e3) / 1e12 if nc else None
+        return {"bound": "tensor", "kernel": "k_contract_tc", "achieved": execd, "peak": peak,
+                "unit": "TFLOP/s", "frac": execd / peak if execd else None, "traffic": None,
+                "peak_source": "measured cuBLAS BF16 burst (MEASURED_PEAKS.json)"
+                               + ("; TF32 = BF16 x 1.1/2.25 nominal" if form == "tf32x3" else ""),
+                "flops": "executed split-product MMA flops", "launches": nc,
+                "avg_launch_ms": msc / nc if nc else None}
 
     clk = ClockSampler(local)
-    ctx, B, ms, prof, launches = measure("fp64", 6, clk)
-    value = world * blocks_per_step * args.steps / (ms / 1e3)
+    ctx, outs, ms, prof, launches = measure(head, clk)
+    value = job_throughput(world, blocks_per_step, args.steps, ms / 1e3)
 
     # roofline of the dominant kernel (the contraction): algorithmic flops / event time
-    n_c, ms_c = prof.get("contract", (0, 0.0))
-    groups = math.ceil(P / 8)
-    flops_per_launch = w.n_t * contraction_flops(w.X, nd, P, pairs) / groups
-    achieved = flops_per_launch / (ms_c / n_c / 1e3) / 1e12 if n_c else None
-    roofline = {
-        "bound": "alu", "kernel": "k_contract_fp64", "achieved": achieved,
-        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-        "traffic": load_traffic("k_contract_fp64"),
-        "peak_source": "derived: 4 FP64 flop/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
-        "flops_per_launch": flops_per_launch,
-        "launches": n_c, "avg_launch_ms": ms_c / n_c if n_c else None,
-    }
+    if head == "fp64":
+        n_c, ms_c = prof.get("contract", (0, 0.0))
+        flops_per_launch = contract_alg * args.steps / n_c if n_c else None
+        achieved = contract_alg * args.steps / (ms_c / 1e3) / 1e12 if n_c else None
+        roofline = {
+            "bound": "alu", "kernel": "k_contract_fp64", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+            "traffic": load_traffic("k_contract_fp64"),
+            "peak_source": "derived: 4 FP64 flop/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
+            "flops_per_launch": flops_per_launch,
+            "launches": n_c, "avg_launch_ms": ms_c / n_c if n_c else None,
+        }
+    else:
+        roofline = tensor_roofline(head, prof)
     kernels = {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / ms if ms else None}
                for k, v in prof.items()}
 
     # the tensor-core forms on the same inputs; error against the FP64 form's blocks
     forms = {}
-    if not args.no_forms:
-        B64 = B.cpu().numpy()
-        nrm = np.linalg.norm(B64)
-        # useful complex GEMM work of the folded contraction: 8 M N K per job, K = 3 pairs X
-        gemm_flops = w.n_t * 8.0 * nd[0] * nd[1] * (P * nd[2]) * (3 * pairs * w.X)
-        for name, prec, prods, nprod, peak in (
-                ("bf16x6", "bf16", 6, 6, BF16_PEAK_TFLOPS), ("bf16x9", "bf16", 9, 9, BF16_PEAK_TFLOPS),
-                ("tf32x3", "tf32x3", 6, 3, TF32_PEAK_TFLOPS), ("bf16x3", "bf16", 3, 3, BF16_PEAK_TFLOPS)):
-            c2, out, t_ms, pr, nl = measure(prec, prods)
-            err = float(np.linalg.norm(out.cpu().numpy() - B64) / nrm)
+    if not args.no_forms and head == "fp64":
+        B64 = [o.cpu().numpy() for o in outs]
+        nrm = math.sqrt(sum(np.linalg.norm(b) ** 2 for b in B64))
+        for name in ("bf16x6", "bf16x9", "tf32x3", "bf16x3"):
+            c2, o2, t_ms, pr, nl = measure(name)
+            err = math.sqrt(sum(np.linalg.norm(a.cpu().numpy() - b) ** 2
+                                for a, b in zip(o2, B64))) / nrm
             nc, msc = pr.get("contract", (0, 0.0))
-            execd = gemm_flops * nprod / (msc / nc / 1e3) / 1e12 if nc else None
             forms[name] = {
-                "blocks_per_s": world * blocks_per_step * args.steps / (t_ms / 1e3),
+                "blocks_per_s": job_throughput(world, blocks_per_step, args.steps, t_ms / 1e3),
                 "ms_per_step": t_ms / args.steps, "gpu_launches": nl,
                 "rel_frobenius_err_vs_fp64_form": err,
                 "speedup_vs_fp64_form": ms / t_ms,
                 "contract_ms_per_launch": msc / nc if nc else None,
-                "tensor_roofline": {"bound": "tensor", "achieved": execd, "peak": peak,
-                                    "unit": "TFLOP/s", "frac": execd / peak if execd else None,
-                                    "flops": "executed split-product MMA flops"},
+                "tensor_roofline": tensor_roofline(name, pr),
                 "kernels": {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / t_ms}
                             for k, v in pr.items()},
             }
             bb.bblock_destroy(c2)
 
-    # end to end through the host-buffer entry point: H2D inputs + compute + D2H blocks
+    # end to end through the public API with host buffers: every step copies the inputs
+    # from pinned host memory, computes, and copies the blocks back
     e2e = None
     if not args.no_e2e:
         hV = torch.from_numpy(inp.V).pin_memory()
-        hphi = [torch.from_numpy(inp.phi[0][i]).pin_memory() for i in range(3)]
-        hB = torch.empty((w.n_t, P, *nd), dtype=torch.complex128).pin_memory()
+        hphi = [[torch.from_numpy(inp.phi[k][i]).pin_memory() for i in range(3)]
+                for k in range(w.n_noise)]
+        hB = [torch.empty(tuple(o.shape), dtype=torch.complex128).pin_memory() for o in outs]
+        if batched:
+            dV = torch.empty_like(V)
+            dphi = [[torch.empty_like(p) for p in ph] for ph in phis]
+            douts = outputs()
+            jobs = [(dV[t], dphi[k][0][t], dphi[k][1][t], dphi[k][2][t], douts[k][t])
+                    for k in range(w.n_noise) for t in range(w.n_t)]
+
+            def e2e_step():
+                with torch.cuda.stream(stream):
+                    dV.copy_(hV, non_blocking=True)
+                    for k in range(w.n_noise):
+                        for i in range(3):
+                            dphi[k][i].copy_(hphi[k][i], non_blocking=True)
+                bb.bblock_compute_batch(ctx, jobs, inp.momenta, inp.spins, inp.coeffs,
+                                        stream=stream)
+                with torch.cuda.stream(stream):
+                    for k in range(w.n_noise):
+                        hB[k].copy_(douts[k], non_blocking=True)
+                stream.synchronize()
+        else:
+            def e2e_step():
+                bb.bblock_compute_host(ctx, hV, *hphi[0], inp.momenta, inp.spins, inp.coeffs,
+                                       hB[0], stream)
         for _ in range(max(1, args.warmup // 2)):
-            bb.bblock_compute_host(ctx, hV, *hphi, inp.momenta, inp.spins, inp.coeffs, hB, stream)
+            e2e_step()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            bb.bblock_compute_host(ctx, hV, *hphi, inp.momenta, inp.spins, inp.coeffs, hB, stream)
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        assert np.array_equal(hB.numpy(), B.cpu().numpy()), "host and device entry points differ"
-        h2d = hV.numel() * 16 + sum(p.numel() * 16 for p in hphi)
-        e2e = {"value": world * blocks_per_step * args.steps / dt, "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": hB.numel() * 16}
+            e2e_step()
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        for h, o in zip(hB, outs):
+            assert np.array_equal(h.numpy(), o.cpu().numpy()), "host and device paths differ"
+        h2d = hV.numel() * 16 + sum(p.numel() * 16 for ph in hphi for p in ph)
+        e2e = {"value": job_throughput(world, blocks_per_step, args.steps, dt), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": sum(h.numel() * 16 for h in hB)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -393,21 +477,24 @@ def run_ours(args):
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        total_flops = w.n_t * (contraction_flops(w.X, nd, P, pairs) +
-                               projection_flops(w.X, w.n_ev, nd, n_alpha, n_beta, pairs))
+        nd0 = inp.ndil[0]
+        field_bytes = sum(3 * w.X * 16 * (n_alpha * nd[0] + n_beta * nd[1] + pairs * nd[2])
+                          for nd in job_nd)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic (seeded, workloads.py)",
-            "config": {"workload": w.name, "L": w.L, "X": w.X, "n_ev": w.n_ev, "ndil": nd[0],
-                       "n_t": w.n_t, "n_mom": P, "n_spin": len(inp.spins), "spin_pairs": pairs,
-                       "form": "fp64", "blocks_per_step_per_gpu": blocks_per_step,
+            "dtype": "f64" if head == "fp64" else ("tf32" if head == "tf32x3" else "bf16"),
+            "data": "synthetic (seeded, workloads.py)",
+            "config": {"workload": w.name, "L": w.L, "X": w.X, "n_ev": w.n_ev,
+                       "ndil": nd0[0] if not batched else sorted({nd[0] for nd in inp.ndil}),
+                       "n_t": w.n_t, "n_noise": w.n_noise, "n_mom": P,
+                       "n_spin": len(inp.spins), "spin_pairs": pairs, "form": head,
+                       "blocks_per_step_per_gpu": blocks_per_step,
                        "l2": "inputs larger than L2 (V %.0f MB, fields %.0f MB per step)" % (
-                           inp.V.nbytes / 1e6, 3 * w.X * 16 * w.n_t *
-                           (n_alpha * nd[0] + n_beta * nd[1] + pairs * nd[2]) / 1e6),
+                           inp.V.nbytes / 1e6, field_bytes / 1e6),
                        "parallelism": f"{world} independent GPU(s), no collective"},
-            "algorithmic_tflops": total_flops * args.steps / (ms / 1e3) / 1e12,
+            "algorithmic_tflops": (contract_alg + project_alg) * args.steps / (ms / 1e3) / 1e12,
             "gpu_launches": launches,
             "kernels": kernels,
             "roofline": roofline,

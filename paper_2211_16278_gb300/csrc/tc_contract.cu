@@ -61,12 +61,15 @@ __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint32_t a) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
+// A waiting thread is suspended until the phase completes or kSuspendNs pass, so idle
+// roles (the epilogue between drains, the MMA thread between stages) take no issue slots.
+constexpr uint32_t kSuspendNs = 1000000;
 __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       "selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+      : "=r"(ok) : "r"(a), "r"(parity), "r"(kSuspendNs) : "memory");
   return ok != 0;
 }
 __device__ __forceinline__ void named_bar(int id, int n) {
@@ -284,7 +287,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_full[s]), R::kProdThreads / 32);   // one arrival per producer warp
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -348,14 +351,17 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
         const int p = row_ok ? n / nd3 : 0, d3 = row_ok ? n - p * nd3 : 0;
         off1 = d3; s1 = nd3; pidx = p;
       }
-      // all producers have passed the previous unit's last stage barrier, so the pointer
-      // table can be rewritten; the barrier below publishes it
+      // Producer warps run their stages independently; at a unit boundary they meet twice:
+      // once so that no warp still reads the previous unit's pointer table while it is
+      // rewritten, once to publish the new table. (bar.sync is warp-aligned: reconverge
+      // every warp before it.)
+      __syncwarp();
+      named_bar(kBarProd, R::kProdThreads);
       if (pt < np) {
         s_q1[pt] = J.q1[prm.a_slot[pt]];
         s_q2[pt] = J.q2[prm.b_slot[pt]];
         s_q3[pt] = J.q3[pt];
       }
-      // bar.sync is warp-aligned: reconverge every warp before it
       __syncwarp();
       named_bar(kBarProd, R::kProdThreads);
       const double2* phase_p = prm.phase + (size_t)pidx * prm.X;
@@ -440,10 +446,11 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
             split_store8<TF32, LEVELS>(im[c], di);
           }
         }
+        // every lane's core-matrix stores are made visible to the tensor core's (async)
+        // proxy; once the whole warp has fenced, one lane arrives for the warp
         fence_async_smem();
         __syncwarp();
-        named_bar(kBarProd, R::kProdThreads);
-        if (pt == 0) mbar_arrive(smem_u32(&bar_full[slot]));
+        if (lane == 0) mbar_arrive(smem_u32(&bar_full[slot]));
         __syncwarp();
       }
     }
