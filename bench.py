@@ -173,28 +173,42 @@ class ClockSampler:
 # ------------------------------------------------------------------ CPU oracle sample
 
 def oracle_sample(inp, target_s: float):
-    """Time the CPU FP64 oracle on a bounded sample of the workload: time slice 0, all
-    momenta, the first n_thr values of d1 (the oracle's OpenMP loop runs over d1, so each
-    thread gets one), the first k values of d2, all d3. Returns (blocks/s, threads, text)."""
+    """Time the CPU FP64 oracle on a bounded sample of the workload.
+
+    The oracle's OpenMP loop runs over d1, so the sample grows in steps of one d1 value per
+    thread: first over d2 values, then over further d1 blocks, then over time slices,
+    until it is about ``target_s`` seconds of CPU work. All momenta and all d3 are always
+    included. Returns (blocks/s, threads, text)."""
     import oracle
     w = inp.workload
     nd = inp.ndil[0]
-    phis = [inp.phi[0][i][0] for i in range(3)]
+    P = len(inp.momenta)
+    n_t = inp.V.shape[0]
     n1 = max(1, min(nd[0], oracle.num_threads()))
-    d1s, all3 = list(range(n1)), list(range(nd[2]))
+    all3 = list(range(nd[2]))
 
-    def run(k):
-        t0 = time.perf_counter()
-        oracle.bblock_sampled(w.L, inp.V[0], *phis, inp.momenta, inp.spins, inp.coeffs,
-                              d1s, list(range(k)), all3)
-        return time.perf_counter() - t0
+    def run(t, d1s, d2s):
+        oracle.bblock_sampled(w.L, inp.V[t], *[inp.phi[0][i][t] for i in range(3)],
+                              inp.momenta, inp.spins, inp.coeffs, d1s, d2s, all3)
 
-    t1 = run(1)
-    k = int(max(1, min(nd[1], round(target_s / max(t1, 1e-3)))))
-    tk = run(k) if k > 1 else t1
-    blocks = len(inp.momenta) * n1 * k / (nd[0] * nd[1])
-    text = (f"time slice 0, {len(inp.momenta)} momenta, d1 in [0,{n1}), d2 in [0,{k}) of "
-            f"{nd[1]}, all {nd[2]} d3 = {blocks:.5f} blocks in {tk:.2f} s on {n1} threads")
+    t0 = time.perf_counter()
+    run(0, list(range(n1)), [0])                 # one d1 block x one d2 value
+    t_unit = max(time.perf_counter() - t0, 1e-3)
+    units = max(1, round(target_s / t_unit))
+    k2 = min(nd[1], units)
+    m1 = min(-(-nd[0] // n1), max(1, round(units / k2)))
+    d1s = list(range(min(nd[0], m1 * n1)))
+    n_ts = 1
+    if len(d1s) == nd[0] and k2 == nd[1]:
+        n_ts = min(n_t, max(1, round(units / (k2 * m1))))
+    t0 = time.perf_counter()
+    for t in range(n_ts):
+        run(t, d1s, list(range(k2)))
+    tk = time.perf_counter() - t0
+    blocks = n_ts * P * len(d1s) * k2 / (nd[0] * nd[1])
+    text = (f"{n_ts} time slice(s), {P} momenta, d1 in [0,{len(d1s)}) of {nd[0]}, d2 in "
+            f"[0,{k2}) of {nd[1]}, all {nd[2]} d3 = {blocks:.4f} blocks in {tk:.2f} s on "
+            f"{n1} threads")
     return blocks / tk, n1, text
 
 
@@ -206,7 +220,7 @@ def run_reference(args):
         return 0
     import oracle
     w = workloads.WORKLOADS[args.workload]
-    inp = workloads.generate(w, n_t=1)
+    inp = workloads.generate(w, n_t=4)
     oracle.build()
     vals, sample = [], ""
     per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
@@ -300,6 +314,8 @@ def run_ours(args):
         import dataclasses
         w = dataclasses.replace(w, n_t=args.n_t)
     batched = w.n_noise > 1
+    # the committed DRAM-traffic captures are of the default workload at full size
+    default_shape = w.name == WORKLOAD and args.n_t is None
     head = args.form or ("bf16x6" if batched else "fp64")
     inp = rank_inputs(w, rank)
     P = len(inp.momenta)
@@ -372,11 +388,14 @@ def run_ours(args):
 
     def tensor_roofline(form, prof):
         nprod, peak = FORMS[form][2:]
+        # DRAM bytes per launch were captured for the BF16x6 variant on this workload
+        traffic = (load_traffic("k_contract_tc")
+                   if form == "bf16x6" and default_shape else None)
         nc, msc = prof.get("contract", (0, 0.0))
         # executed MMA flops of the timed steps / the contraction launches' summed time
         execd = gemm_flops * nprod * args.steps / (msc / 1e3) / 1e12 if nc else None
         return {"bound": "tensor", "kernel": "k_contract_tc", "achieved": execd, "peak": peak,
-                "unit": "TFLOP/s", "frac": execd / peak if execd else None, "traffic": None,
+                "unit": "TFLOP/s", "frac": execd / peak if execd else None, "traffic": traffic,
                 "peak_source": "measured cuBLAS BF16 burst (MEASURED_PEAKS.json)"
                                + ("; TF32 = BF16 x 1.1/2.25 nominal" if form == "tf32x3" else ""),
                 "flops": "executed split-product MMA flops", "launches": nc,
@@ -395,7 +414,7 @@ def run_ours(args):
             "bound": "alu", "kernel": "k_contract_fp64", "achieved": achieved,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-            "traffic": load_traffic("k_contract_fp64"),
+            "traffic": load_traffic("k_contract_fp64") if default_shape else None,
             "peak_source": "derived: 4 FP64 flop/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
             "flops_per_launch": flops_per_launch,
             "launches": n_c, "avg_launch_ms": ms_c / n_c if n_c else None,
@@ -473,7 +492,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = oracle_sample(workloads.generate(w, n_t=1), args.cpu_seconds)
+        v, cores, sample = oracle_sample(workloads.generate(w, n_t=4), args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
