@@ -76,7 +76,7 @@ def parse_args():
                     help="target CPU seconds of one oracle sample")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the tensor-core forms (time the FP64 form only)")
-    ap.add_argument("--form", choices=["fp64", "bf16x6", "bf16x9", "tf32x3", "bf16x3"],
+    ap.add_argument("--form", choices=["fp64", "df64", "bf16x6", "bf16x9", "tf32x3", "bf16x3"],
                     default=None, help="form of the headline number (default: fp64; bf16x6 "
                     "for the batched workload)")
     ap.add_argument("--n-t", type=int, default=None,
@@ -284,8 +284,22 @@ def job_throughput(world: int, blocks_per_step: int, steps: int, seconds: float)
     return world * blocks_per_step * steps / seconds
 
 
+# Peak of the FP32 pipe (the double-float form's bound): 128 FP32 instructions/clk/SM x 152
+# SMs x 2070 MHz, in tera-instructions per second.
+FP32_INST_PEAK = 128 * 152 * 2.070e9 / 1e12
+
+
+def contraction_df_inst(X, nd, P, pairs):
+    """FP32 instructions of the double-float contraction's inner loops per (time slice,
+    noise triple): 12 per double-float FMA (exact product error, TwoSum, lazy error sum),
+    three per (pair, colour) in the singlet, four per momentum, 16 for the singlet's real and
+    imaginary parts; per (d1, d2, d3, x)."""
+    d1, d2, d3 = nd
+    return (108.0 * pairs + 16.0 + 48.0 * P) * d1 * d2 * d3 * X
+
+
 FORMS = {  # name: (precision, bf16 products, MMA piece products, tensor peak TFLOP/s)
-    "fp64": ("fp64", 6, 0, None),
+    "fp64": ("fp64", 6, 0, None), "df64": ("df64", 6, 0, None),
     "bf16x6": ("bf16", 6, 6, BF16_PEAK_TFLOPS), "bf16x9": ("bf16", 9, 9, BF16_PEAK_TFLOPS),
     "tf32x3": ("tf32x3", 6, 3, TF32_PEAK_TFLOPS), "bf16x3": ("bf16", 3, 3, BF16_PEAK_TFLOPS),
 }
@@ -401,6 +415,20 @@ def run_ours(args):
                 "flops": "executed split-product MMA flops", "launches": nc,
                 "avg_launch_ms": msc / nc if nc else None}
 
+    def df_roofline(prof):
+        nc, msc = prof.get("contract", (0, 0.0))
+        inst = sum(contraction_df_inst(w.X, nd, P, pairs) for nd in job_nd)
+        ach = inst * args.steps / (msc / 1e3) / 1e12 if nc else None
+        flops = contract_alg * args.steps / (msc / 1e3) / 1e12 if nc else None
+        return {"bound": "alu", "kernel": "k_contract_df", "achieved": ach,
+                "peak": FP32_INST_PEAK, "unit": "T FP32-inst/s",
+                "frac": ach / FP32_INST_PEAK if ach else None,
+                "traffic": load_traffic("k_contract_df") if default_shape else None,
+                "peak_source": "derived: 128 FP32 instructions/clk/SM x 152 SMs x 2070 MHz",
+                "flops": "modelled FP32 instructions of the double-float inner loops",
+                "complex_count_tflops": flops, "launches": nc,
+                "avg_launch_ms": msc / nc if nc else None}
+
     clk = ClockSampler(local)
     ctx, outs, ms, prof, launches = measure(head, clk)
     value = job_throughput(world, blocks_per_step, args.steps, ms / 1e3)
@@ -429,7 +457,7 @@ def run_ours(args):
     if not args.no_forms and head == "fp64":
         B64 = [o.cpu().numpy() for o in outs]
         nrm = math.sqrt(sum(np.linalg.norm(b) ** 2 for b in B64))
-        for name in ("bf16x6", "bf16x9", "tf32x3", "bf16x3"):
+        for name in ("df64", "bf16x6", "bf16x9", "tf32x3", "bf16x3"):
             c2, o2, t_ms, pr, nl = measure(name)
             err = math.sqrt(sum(np.linalg.norm(a.cpu().numpy() - b) ** 2
                                 for a, b in zip(o2, B64))) / nrm
@@ -440,7 +468,8 @@ def run_ours(args):
                 "rel_frobenius_err_vs_fp64_form": err,
                 "speedup_vs_fp64_form": ms / t_ms,
                 "contract_ms_per_launch": msc / nc if nc else None,
-                "tensor_roofline": tensor_roofline(name, pr),
+                ("alu_roofline" if name == "df64" else "tensor_roofline"):
+                    df_roofline(pr) if name == "df64" else tensor_roofline(name, pr),
                 "kernels": {k: {"launches": v[0], "total_ms": v[1], "share": v[1] / t_ms}
                             for k, v in pr.items()},
             }

@@ -27,7 +27,7 @@ ERRORS = {
     -6: "BBLOCK_ERR_DEVICE_FLAG",
     -7: "BBLOCK_ERR_TOO_LARGE",
 }
-PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16": 2}
+PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16": 2, "df64": 3}
 
 # Every symbol include/bblock.h declares.
 EXPORTED = (

@@ -126,6 +126,11 @@ int cuda_fail(bblock_ctx* c, cudaError_t e, const char* what) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// The FP64 and double-float forms share fields, tiles, units and the FP64 reduction.
+bool fp64_like(const bblock_config& cfg) {
+  return cfg.precision == BBLOCK_FP64 || cfg.precision == BBLOCK_DF64;
+}
+
 // Workspace one wave of jobs may take: the caller's limit, else half the free memory seen at
 // creation (at most 96 GiB). A job larger than the budget still runs, alone in its wave.
 size_t wave_budget(const bblock_ctx* c) { return c->opt_wave_bytes ? c->opt_wave_bytes : c->ws_budget; }
@@ -567,7 +572,8 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
   if (sp.n_pairs > kMaxPairs) return fail(c, BBLOCK_ERR_UNSUPPORTED, "more than %d spin pairs", kMaxPairs);
   rc = ensure_phase(c, momenta, n_mom, s);
   if (rc) return rc;
-  if (c->cfg.precision != BBLOCK_FP64) return run_jobs_tc(c, jobs, sp, n_mom, per_mom, s);
+  if (!fp64_like(c->cfg)) return run_jobs_tc(c, jobs, sp, n_mom, per_mom, s);
+  const bool df = c->cfg.precision == BBLOCK_DF64;
 
   const int X = c->X, rows = c->rows, n_ev = c->cfg.n_ev;
   const int n3_fields = sp.n_pairs * sp.n_coef_sets;
@@ -698,7 +704,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
     const ProjField* d_fields = reinterpret_cast<const ProjField*>(c->d_tab);
 
     CK(c, timed_launch(c, K_PROJECT, s, [&] {
-      return launch_project_fp64(d_fields, (int)fields.size(), rows, n_ev, max_ndf, s);
+      return launch_project_fp64(d_fields, (int)fields.size(), rows, n_ev, max_ndf, df, s);
     }));
 
     ContractParams prm{};
@@ -717,14 +723,18 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       for (int p = 0; p < n_mom; ++p) {
         prm.jobs = reinterpret_cast<const ContractJob*>(c->d_tab + fbytes + jbytes * p);
         prm.p0 = p;
-        CK(c, timed_launch(c, K_CONTRACT, s, [&] { return launch_contract_fp64(prm, 1, tl.rn, grid, s); }));
+        CK(c, timed_launch(c, K_CONTRACT, s, [&] {
+          return df ? launch_contract_df(prm, 1, tl.rn, grid, s) : launch_contract_fp64(prm, 1, tl.rn, grid, s);
+        }));
       }
     } else {
       prm.jobs = reinterpret_cast<const ContractJob*>(c->d_tab + fbytes);
       for (int p0 = 0; p0 < n_mom; p0 += kMaxPGroup) {
         const int Pg = std::min(kMaxPGroup, n_mom - p0);
         prm.p0 = p0;
-        CK(c, timed_launch(c, K_CONTRACT, s, [&] { return launch_contract_fp64(prm, Pg, tl.rn, grid, s); }));
+        CK(c, timed_launch(c, K_CONTRACT, s, [&] {
+          return df ? launch_contract_df(prm, Pg, tl.rn, grid, s) : launch_contract_fp64(prm, Pg, tl.rn, grid, s);
+        }));
       }
     }
     CK(c, timed_launch(c, K_REDUCE, s, [&] {
@@ -852,7 +862,7 @@ CallPlan plan_call(const bblock_ctx* c, int n_t, const int nd[3], int n_mom, int
                    int nc_opt, int chunk_opt, int slabs_opt) {
   CallPlan pl;
   const int X = c->X;
-  if (c->cfg.precision == BBLOCK_FP64) {
+  if (fp64_like(c->cfg)) {
     const int P = std::min(n_mom, kMaxPGroup);
     const Fp64Tile tl = fp64_tile_for(P);
     const int xc = fp64_sites_per_chunk(pairs);
@@ -889,6 +899,7 @@ CallPlan plan_call(const bblock_ctx* c, int n_t, const int nd[3], int n_mom, int
 
 int form_code(const bblock_config& cfg) {
   if (cfg.precision == BBLOCK_FP64) return 0;
+  if (cfg.precision == BBLOCK_DF64) return 5;
   if (cfg.precision == BBLOCK_TF32X3) return 4;
   return cfg.bf16_products == 3 ? 1 : cfg.bf16_products == 9 ? 3 : 2;
 }
@@ -922,7 +933,7 @@ int bblock_create(bblock_ctx** out, const bblock_config* cfg) {
   const long long X = (long long)cfg->L * cfg->L * cfg->L;
   if (cfg->n_ev < 1 || cfg->n_ev > 3 * X) return BBLOCK_ERR_INVALID_ARG;
   if (cfg->max_ndil < 1 || cfg->max_ndil > 256) return BBLOCK_ERR_INVALID_ARG;
-  if (cfg->precision < BBLOCK_FP64 || cfg->precision > BBLOCK_BF16_SPLIT) return BBLOCK_ERR_INVALID_ARG;
+  if (cfg->precision < BBLOCK_FP64 || cfg->precision > BBLOCK_DF64) return BBLOCK_ERR_INVALID_ARG;
   if (cfg->precision == BBLOCK_BF16_SPLIT && cfg->bf16_products != 3 && cfg->bf16_products != 6 &&
       cfg->bf16_products != 9)
     return BBLOCK_ERR_INVALID_ARG;
@@ -1123,7 +1134,7 @@ int bblock_autotune(bblock_ctx* c, int n_t, const void* V, const void* phi1, con
   const CallPlan base = plan_call(c, n_t, nd, n_mom, sp.n_pairs, 0, 0, 0);
   const int a = std::max(1, base.n_slab);
   const int slab_choices[4] = {0, std::max(1, a / 2), 2 * a, 4 * a};
-  if (c->cfg.precision == BBLOCK_FP64) {
+  if (fp64_like(c->cfg)) {
     for (int k = 0; k < 4; ++k) cand.push_back({0, 0, slab_choices[k]});
   } else {
     for (int nc = 16; nc <= 48; nc += 16)

@@ -1,4 +1,7 @@
-"""GPU parity of the FP64 form against the CPU FP64 oracle (relative Frobenius <= 1e-12).
+"""GPU parity of the FP64-accurate forms against the CPU FP64 oracle (relative Frobenius
+<= 1e-12): the FP64 form (IEEE double on the FP64 pipe) and the double-float form (pairs of
+FP32 on the FP32 pipe). The parity tests run for both forms; the tests of host logic
+(argument checks, empty calls, the host-buffer entry point) use the FP64 form.
 
 All calls go through the C ABI (``paper_2211_16278_gb300.bblock``). Inputs are
 seeded synthetic draws from ``workloads``; expected values come from ``oracle``.
@@ -22,6 +25,11 @@ def torch_cuda():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return torch
+
+
+@pytest.fixture(params=["fp64", "df64"])
+def form(request):
+    return request.param
 
 
 @pytest.fixture(scope="module")
@@ -60,9 +68,9 @@ def oracle_blocks(inp, noise=0, coeffs=None):
                                    inp.momenta, inp.spins, c) for t in range(inp.V.shape[0])])
 
 
-def test_l4_nev8_ndil8_full(bb, torch_cuda):
+def test_l4_nev8_ndil8_full(bb, torch_cuda, form):
     inp = workloads.generate(workloads.WORKLOADS["l4_nev8_ndil8"])
-    got = run_gpu(bb, torch_cuda, inp)
+    got = run_gpu(bb, torch_cuda, inp, form)
     ref = oracle_blocks(inp)
     assert got.shape == ref.shape == (1, 1, 8, 8, 8)
     assert rel(got, ref) <= TOL_FP64
@@ -81,50 +89,50 @@ RAGGED_CASES = [
 
 
 @pytest.mark.parametrize("case", range(len(RAGGED_CASES)))
-def test_ragged_small_shapes(bb, torch_cuda, case):
+def test_ragged_small_shapes(bb, torch_cuda, case, form):
     L, n_ev, nd, n_t, mom, spins, coeffs = RAGGED_CASES[case]
     inp = workloads.custom(L, n_ev, nd, n_t, mom, spins, coeffs, seed=1000 + case)
-    got = run_gpu(bb, torch_cuda, inp)
+    got = run_gpu(bb, torch_cuda, inp, form)
     ref = oracle_blocks(inp)
     assert rel(got, ref) <= TOL_FP64
 
 
-def test_many_momenta_use_several_launch_groups(bb, torch_cuda):
+def test_many_momenta_use_several_launch_groups(bb, torch_cuda, form):
     mom = [(a, b, c) for a in (-1, 0, 1) for b in (0, 1) for c in (0, 1)][:11]
     inp = workloads.custom(3, 6, (4, 5, 6), 1, mom, [(0, 1, 0), (2, 2, 3)], [1.0, -0.5j], seed=7)
-    assert rel(run_gpu(bb, torch_cuda, inp), oracle_blocks(inp)) <= TOL_FP64
+    assert rel(run_gpu(bb, torch_cuda, inp, form), oracle_blocks(inp)) <= TOL_FP64
 
 
-def test_momentum_dependent_spin_coefficients(bb, torch_cuda):
+def test_momentum_dependent_spin_coefficients(bb, torch_cuda, form):
     mom = [(0, 0, 0), (1, 0, 0), (1, 1, 0)]
     spins = [(0, 1, 0), (1, 0, 0), (2, 3, 2)]
     rng = np.random.default_rng(3)
     coeffs = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
     inp = workloads.custom(3, 8, (6, 5, 7), 2, mom, spins, np.ones(3), seed=8)
-    got = run_gpu(bb, torch_cuda, inp, coeffs=coeffs)
+    got = run_gpu(bb, torch_cuda, inp, form, coeffs=coeffs)
     assert rel(got, oracle_blocks(inp, coeffs=coeffs)) <= TOL_FP64
 
 
-def test_all_sixteen_spin_pairs(bb, torch_cuda):
+def test_all_sixteen_spin_pairs(bb, torch_cuda, form):
     spins = [(a, b, (a + b) % 4) for a in range(4) for b in range(4)]
     coeffs = [complex(math.cos(k), math.sin(k)) for k in range(16)]
     inp = workloads.custom(2, 5, (3, 4, 5), 1, [(0, 0, 0), (1, 0, 1)], spins, coeffs, seed=9)
-    assert rel(run_gpu(bb, torch_cuda, inp), oracle_blocks(inp)) <= TOL_FP64
+    assert rel(run_gpu(bb, torch_cuda, inp, form), oracle_blocks(inp)) <= TOL_FP64
 
 
-def test_repeated_triples_fold_into_one_field(bb, torch_cuda):
+def test_repeated_triples_fold_into_one_field(bb, torch_cuda, form):
     spins = [(0, 1, 2), (0, 1, 2), (0, 1, 3), (0, 1, 0), (0, 1, 1)]
     coeffs = [0.25, 0.25, -1.0, 0.5j, 2.0]
     inp = workloads.custom(3, 6, (4, 4, 4), 1, [(0, 0, 0), (0, 1, 0)], spins, coeffs, seed=10)
-    assert rel(run_gpu(bb, torch_cuda, inp), oracle_blocks(inp)) <= TOL_FP64
+    assert rel(run_gpu(bb, torch_cuda, inp, form), oracle_blocks(inp)) <= TOL_FP64
 
 
-def test_deterministic_across_runs(bb, torch_cuda):
+def test_deterministic_across_runs(bb, torch_cuda, form):
     inp = workloads.custom(4, 10, (8, 8, 8), 2, [(0, 0, 0), (1, 0, 0)], [(0, 1, 0)], [1.0], seed=11)
     torch = torch_cuda
-    ctx = bb.bblock_create(4, 10, 8, "fp64")
-    a = run_gpu(bb, torch, inp, ctx=ctx)
-    b = run_gpu(bb, torch, inp, ctx=ctx)
+    ctx = bb.bblock_create(4, 10, 8, form)
+    a = run_gpu(bb, torch, inp, form, ctx=ctx)
+    b = run_gpu(bb, torch, inp, form, ctx=ctx)
     assert np.array_equal(a, b)
     bb.bblock_destroy(ctx)
 
@@ -158,7 +166,7 @@ def test_host_entry_point_matches_device_entry_point(bb, torch_cuda):
     bb.bblock_destroy(ctx)
 
 
-def test_batch_with_uneven_dilution_matches_single_calls(bb, torch_cuda):
+def test_batch_with_uneven_dilution_matches_single_calls(bb, torch_cuda, form):
     torch = torch_cuda
     dev = torch.device("cuda:0")
     L, n_ev = 3, 8
@@ -172,7 +180,7 @@ def test_batch_with_uneven_dilution_matches_single_calls(bb, torch_cuda):
         host.append((V, ph))
         B = torch.zeros((len(mom), *nd), dtype=torch.complex128, device=dev)
         jobs.append((torch.from_numpy(V).to(dev), *[torch.from_numpy(p).to(dev) for p in ph], B))
-    ctx = bb.bblock_create(L, n_ev, 9, "fp64")
+    ctx = bb.bblock_create(L, n_ev, 9, form)
     bb.bblock_compute_batch(ctx, jobs, mom, spins, coeffs)
     bb.bblock_status(ctx)
     for (V, ph), job in zip(host, jobs):
@@ -213,12 +221,12 @@ def test_invalid_arguments_are_rejected(bb, torch_cuda):
 
 # ---------------------------------------------------------------- full-size workload, sampled
 
-def test_l24_nev96_ndil32_sampled_entries(bb, torch_cuda):
+def test_l24_nev96_ndil32_sampled_entries(bb, torch_cuda, form):
     """The benchmarked workload (L=24, N_ev=96, N_dil=32, 8 time slices) at full size;
     sampled (t, d1, d2, d3) entries against the oracle, which evaluates them one by one."""
     w = workloads.WORKLOADS["l24_nev96_ndil32"]
     inp = workloads.generate(w)
-    got = run_gpu(bb, torch_cuda, inp)
+    got = run_gpu(bb, torch_cuda, inp, form)
     assert got.shape == (8, 3, 32, 32, 32)
     d1s, d2s, d3s = [0, 13, 31], [5, 31], [0, 30, 31]
     for t in (0, 7):

@@ -9,16 +9,16 @@ in its default launch configuration: default tiles, CUDA graphs on a created str
 * L = 32, N_ev = 128, N_dil = 64, 5 momenta, 4 spin triples, two of the 16 time slices:
   every form.
 * L = 48, N_ev = 264, N_dil = 64, 7 momenta, 4 spin triples, one of the 4 time slices: the
-  FP64 form and the BF16 split with 6 products.
+  FP64 and double-float forms and the BF16 split with 6 products.
 * L = 32, N_ev = 128, 9 momenta, 6 noise triples with N_dil drawn from {32, 48, 64}, two
   time slices per noise triple: 12 jobs of uneven size in one batched call, in the mixed
-  forms. The call is repeated, so the second call is a CUDA-graph capture and the third a
-  replay; every call is checked.
+  forms and the double-float form. The call is repeated, so the second call is a
+  CUDA-graph capture and the third a replay; every call is checked.
 
-Tolerances are relative Frobenius errors over the sampled entries: 1e-12 for the FP64 form,
-1e-6 for the split forms with 6 or 9 BF16 products and for TF32x3, and 1e-4 for the BF16
-split with 3 products. The last form's dropped products are about 3 * 2^-16 relative, so it
-is reported rather than held to 1e-6.
+Tolerances are relative Frobenius errors over the sampled entries: 1e-12 for the FP64 and
+double-float forms, 1e-6 for the split forms with 6 or 9 BF16 products and for TF32x3, and
+1e-4 for the BF16 split with 3 products. The last form's dropped products are about
+3 * 2^-16 relative, so it is reported rather than held to 1e-6.
 """
 import numpy as np
 import pytest
@@ -28,7 +28,8 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 
-FORMS = {"fp64": ("fp64", 6, 1e-12), "bf16x6": ("bf16", 6, 1e-6), "bf16x9": ("bf16", 9, 1e-6),
+FORMS = {"fp64": ("fp64", 6, 1e-12), "df64": ("df64", 6, 1e-12),
+         "bf16x6": ("bf16", 6, 1e-6), "bf16x9": ("bf16", 9, 1e-6),
          "tf32x3": ("tf32x3", 6, 1e-6), "bf16x3": ("bf16", 3, 1e-4)}
 
 
@@ -85,7 +86,7 @@ def test_l32_nev128_ndil64_sampled(env, l32_inputs, form):
         assert err <= tol
 
 
-@pytest.mark.parametrize("form", ["fp64", "bf16x6"])
+@pytest.mark.parametrize("form", ["fp64", "df64", "bf16x6"])
 def test_l48_nev264_ndil64_sampled(env, form):
     torch, bb = env
     precision, products, tol = FORMS[form]
@@ -109,7 +110,7 @@ def test_l48_nev264_ndil64_sampled(env, form):
     assert err <= tol
 
 
-@pytest.mark.parametrize("form", ["bf16x6", "tf32x3"])
+@pytest.mark.parametrize("form", ["bf16x6", "tf32x3", "df64"])
 def test_l32_batch_uneven_dilution_sampled(env, form):
     torch, bb = env
     precision, products, tol = FORMS[form]

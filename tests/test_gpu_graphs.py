@@ -34,7 +34,7 @@ def setup(torch, inp):
     return (torch.from_numpy(inp.V).to(dev), [torch.from_numpy(inp.phi[0][i]).to(dev) for i in range(3)])
 
 
-@pytest.mark.parametrize("precision,products", [("fp64", 6), ("bf16", 6), ("tf32x3", 6)])
+@pytest.mark.parametrize("precision,products", [("fp64", 6), ("df64", 6), ("bf16", 6), ("tf32x3", 6)])
 def test_graph_replay_is_bitwise_equal_to_plain_launches(env, precision, products):
     torch, bb = env
     inp = workloads.custom(4, 10, (9, 8, 12), 2, [(0, 0, 0), (1, 0, 0), (1, 1, 0)],
@@ -120,7 +120,7 @@ def test_bad_option_values_are_rejected(env):
     bb.bblock_destroy(ctx)
 
 
-@pytest.mark.parametrize("precision,products,tol", [("fp64", 6, 1e-12), ("bf16", 6, 1e-6),
+@pytest.mark.parametrize("precision,products,tol", [("fp64", 6, 1e-12), ("df64", 6, 1e-12), ("bf16", 6, 1e-6),
                                                     ("tf32x3", 6, 1e-6)])
 def test_multi_wave_batch_graph_replay(env, precision, products, tol):
     """A batch that runs as several waves of launches (a small workspace budget per wave),
