@@ -66,8 +66,8 @@ struct bblock_ctx {
 };
 
 namespace {
-enum KernelKind { K_PHASE = 0, K_PROJECT, K_CONTRACT, K_REDUCE, K_COUNT };
-const char* const kKernelNames[K_COUNT] = {"phase", "project", "contract", "reduce"};
+enum KernelKind { K_PHASE = 0, K_PROJECT, K_CONTRACT, K_REDUCE, K_CONVERT, K_COUNT };
+const char* const kKernelNames[K_COUNT] = {"phase", "project", "contract", "reduce", "convert"};
 
 cudaEvent_t take_event(bblock_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -583,11 +583,17 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
   const int ctas = fp64_contract_ctas_per_sm(P_launch, tl.rn, sp.n_pairs) * c->num_sms;
   const int max_slabs = 64;
 
-  // bytes per job: fields + partials at the largest slab count
+  // double-float inputs of a job: V and the three phi_i as float4 planes
+  auto df_in_bytes = [&](const JobIn& j) -> size_t {
+    if (!df) return 0;
+    return align_up((size_t)rows * n_ev * sizeof(float4), 256) +
+           align_up((size_t)4 * n_ev * (j.nd[0] + j.nd[1] + j.nd[2]) * sizeof(float4), 256);
+  };
+  // bytes per job: fields + partials at the largest slab count (+ double-float inputs)
   auto job_bytes = [&](const JobIn& j, int n_slab) {
     size_t f = (size_t)rows * (sp.n1 * j.nd[0] + sp.n2 * j.nd[1] + n3_fields * j.nd[2]) * sizeof(double2);
     size_t p = (size_t)n_slab * n_mom * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(double2);
-    return align_up(f, 256) + align_up(p, 256);
+    return align_up(f, 256) + align_up(p, 256) + df_in_bytes(j);
   };
 
   size_t job_idx = 0;
@@ -626,15 +632,39 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
     // field and job tables
     std::vector<ProjField> fields;
     std::vector<std::vector<ContractJob>> cjobs(sp.n_coef_sets, std::vector<ContractJob>(nj));
+    std::vector<DfConvSeg> segs;
+    long long max_seg = 0;
     char* ws = c->d_ws;
     long long unit = 0;
     for (int k = 0; k < nj; ++k) {
       const JobIn& j = jobs[job_idx + k];
       char* base = ws;
+      // double-float form: the job's inputs are converted to float4 planes first
+      const double2* Vin = j.V;
+      const double2* phin[3] = {j.phi[0], j.phi[1], j.phi[2]};
+      if (df) {
+        char* dbase = base;
+        auto add_seg = [&](const double2* src, long long n) -> const double2* {
+          float4* dst = reinterpret_cast<float4*>(dbase);
+          segs.push_back(DfConvSeg{src, dst, n});
+          max_seg = std::max(max_seg, n);
+          dbase += align_up((size_t)n * sizeof(float4), 256);
+          return reinterpret_cast<const double2*>(dst);
+        };
+        Vin = add_seg(j.V, (long long)rows * n_ev);
+        char* phi_base = dbase;
+        for (int i = 0; i < 3; ++i) {
+          phin[i] = reinterpret_cast<const double2*>(phi_base);
+          segs.push_back(DfConvSeg{j.phi[i], reinterpret_cast<float4*>(phi_base), 4LL * n_ev * j.nd[i]});
+          max_seg = std::max(max_seg, 4LL * n_ev * j.nd[i]);
+          phi_base += (size_t)4 * n_ev * j.nd[i] * sizeof(float4);
+        }
+        base += df_in_bytes(j);
+      }
       auto add_field = [&](const double2* phi, int nd, int n_terms, const int* offs,
                            const double2* w) -> double2* {
         ProjField f{};
-        f.V = j.V;
+        f.V = Vin;
         f.phi = phi;
         f.q = reinterpret_cast<double2*>(base);
         f.nd = nd;
@@ -649,11 +679,11 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       const double2* q2[4] = {};
       for (int sl = 0; sl < sp.n1; ++sl) {
         int off = sp.alpha_of1[sl] * n_ev;
-        q1[sl] = add_field(j.phi[0], j.nd[0], 1, &off, &one);
+        q1[sl] = add_field(phin[0], j.nd[0], 1, &off, &one);
       }
       for (int sl = 0; sl < sp.n2; ++sl) {
         int off = sp.beta_of2[sl] * n_ev;
-        q2[sl] = add_field(j.phi[1], j.nd[1], 1, &off, &one);
+        q2[sl] = add_field(phin[1], j.nd[1], 1, &off, &one);
       }
       std::vector<std::vector<const double2*>> q3(sp.n_coef_sets, std::vector<const double2*>(sp.n_pairs));
       for (int set = 0; set < sp.n_coef_sets; ++set)
@@ -663,7 +693,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
           int offs[kMaxTerms];
           double2 w[kMaxTerms];
           for (size_t t = 0; t < tlist.size(); ++t) { offs[t] = tlist[t].first * n_ev; w[t] = tlist[t].second; }
-          q3[set][pr] = add_field(j.phi[2], j.nd[2], (int)tlist.size(), offs, w);
+          q3[set][pr] = add_field(phin[2], j.nd[2], (int)tlist.size(), offs, w);
         }
       base = c->d_ws + align_up((size_t)(base - c->d_ws), 256);
       double2* partial = reinterpret_cast<double2*>(base);
@@ -693,18 +723,30 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       if (!within_workspace(c, cj.partial, (size_t)n_slab * n_mom * cj.nd1 * cj.nd2 * cj.nd3 * sizeof(double2)))
         return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: partial block outside the workspace");
     }
+    for (const DfConvSeg& g : segs)
+      if (!within_workspace(c, g.dst, (size_t)g.n * sizeof(float4)))
+        return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: converted input outside the workspace");
     const size_t fbytes = align_up(fields.size() * sizeof(ProjField), 256);
     const size_t jbytes = align_up((size_t)nj * sizeof(ContractJob), 256);
-    std::vector<char> tab(fbytes + jbytes * sp.n_coef_sets);
+    const size_t sofs = fbytes + jbytes * sp.n_coef_sets;
+    std::vector<char> tab(sofs + segs.size() * sizeof(DfConvSeg));
     memcpy(tab.data(), fields.data(), fields.size() * sizeof(ProjField));
     for (int set = 0; set < sp.n_coef_sets; ++set)
       memcpy(tab.data() + fbytes + jbytes * set, cjobs[set].data(), (size_t)nj * sizeof(ContractJob));
+    if (!segs.empty()) memcpy(tab.data() + sofs, segs.data(), segs.size() * sizeof(DfConvSeg));
     rc = upload_tables(c, tab.data(), tab.size(), s);
     if (rc) return rc;
     const ProjField* d_fields = reinterpret_cast<const ProjField*>(c->d_tab);
 
+    if (df) {
+      CK(c, timed_launch(c, K_CONVERT, s, [&] {
+        return launch_convert_df(reinterpret_cast<const DfConvSeg*>(c->d_tab + sofs),
+                                 (int)segs.size(), max_seg, s);
+      }));
+    }
     CK(c, timed_launch(c, K_PROJECT, s, [&] {
-      return launch_project_fp64(d_fields, (int)fields.size(), rows, n_ev, max_ndf, df, s);
+      return df ? launch_project_df(d_fields, (int)fields.size(), rows, n_ev, max_ndf, s)
+                : launch_project_fp64(d_fields, (int)fields.size(), rows, n_ev, max_ndf, s);
     }));
 
     ContractParams prm{};

@@ -124,11 +124,25 @@ cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab,
 
 cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, cudaStream_t s);
 cudaError_t launch_project_fp64(const ProjField* d_fields, int n_fields, int rows, int n_ev,
-                                int max_nd, bool df_out, cudaStream_t s);
+                                int max_nd, cudaStream_t s);
 cudaError_t launch_contract_fp64(const ContractParams& p, int P, int rn, int grid, cudaStream_t s);
 // Double-float form: same units, tiles, shared memory and partial layout as the FP64
 // contraction; fields hold double-float pairs (float4 per complex element).
 cudaError_t launch_contract_df(const ContractParams& p, int P, int rn, int grid, cudaStream_t s);
+
+// One input array of a call converted to double-float planes: n complex128 elements
+// from src to float4 (re.h, re.l, im.h, im.l) at dst.
+struct DfConvSeg {
+  const double2* src;
+  float4* dst;
+  long long n;
+};
+cudaError_t launch_convert_df(const DfConvSeg* d_segs, int n_segs, long long max_n,
+                              cudaStream_t s);
+// Eq. (2) in double-float arithmetic: the fields' V and phi point to converted float4
+// planes (cast to const double2*), q receives float4 double-float elements.
+cudaError_t launch_project_df(const ProjField* d_fields, int n_fields, int rows, int n_ev,
+                              int max_nd, cudaStream_t s);
 int fp64_contract_ctas_per_sm(int P, int rn, int n_pairs);
 cudaError_t launch_reduce_slabs(const ContractJob* d_jobs, int n_jobs, int n_slab, int P_total,
                                 long long max_elems, cudaStream_t s);

@@ -18,7 +18,6 @@
 //     9*n_pairs + 2 + 4*P FP64 operations instead of n_pairs*(12 + 4P);
 //   * the diquark of a (d1,d2) tile is built once per site and reused for every d3.
 #include "bblock_internal.h"
-#include "dfloat.cuh"
 
 namespace bb {
 
@@ -61,9 +60,6 @@ cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, 
 
 constexpr int PBM = 64, PBN = 32, PBK = 16;
 
-// DF: write each element as a double-float pair per component (float4: re.h, re.l, im.h,
-// im.l; the same 16 bytes as the double2 it replaces) for the double-float contraction.
-template <bool DF>
 __global__ void __launch_bounds__(kThreads) k_project_fp64(const ProjField* __restrict__ fields,
                                                            int rows, int n_ev) {
   __shared__ double Ar[PBK][PBM], Ai[PBK][PBM], As[PBK][PBM];
@@ -142,28 +138,19 @@ __global__ void __launch_bounds__(kThreads) k_project_fp64(const ProjField* __re
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int col = n0 + tn + 8 * j;
-      if (col >= nd) continue;
-      const double re = k1[i][j] - k3[i][j], im = k1[i][j] + k2[i][j];
-      if (DF) {
-        const dfloat r = df_from_double(re), m = df_from_double(im);
-        reinterpret_cast<float4*>(F.q)[(size_t)row * nd + col] = make_float4(r.h, r.l, m.h, m.l);
-      } else {
-        F.q[(size_t)row * nd + col] = make_double2(re, im);
-      }
+      if (col < nd)
+        F.q[(size_t)row * nd + col] = make_double2(k1[i][j] - k3[i][j], k1[i][j] + k2[i][j]);
     }
   }
 }
 
 cudaError_t launch_project_fp64(const ProjField* d_fields, int n_fields, int rows, int n_ev,
-                                int max_nd, bool df_out, cudaStream_t s) {
+                                int max_nd, cudaStream_t s) {
   if (n_fields == 0 || rows == 0) return cudaSuccess;
   for (int f0 = 0; f0 < n_fields; f0 += 65535) {  // grid.z limit
     const int nf = n_fields - f0 < 65535 ? n_fields - f0 : 65535;
     dim3 grid((rows + PBM - 1) / PBM, (max_nd + PBN - 1) / PBN, nf);
-    if (df_out)
-      k_project_fp64<true><<<grid, kThreads, 0, s>>>(d_fields + f0, rows, n_ev);
-    else
-      k_project_fp64<false><<<grid, kThreads, 0, s>>>(d_fields + f0, rows, n_ev);
+    k_project_fp64<<<grid, kThreads, 0, s>>>(d_fields + f0, rows, n_ev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

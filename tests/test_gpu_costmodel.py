@@ -119,10 +119,11 @@ def test_model_ranking_gains_over_exhaustive_search(env):
         bb.bblock_destroy(d[0])
 
 
-def test_fp64_autotune_keeps_parity(env):
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_fp64_accurate_autotune_keeps_parity(env, precision):
     torch, bb = env
     inp, V, phis, B = _workload(torch, 6, 12, 10, 2, [(0, 0, 0), (1, 0, 0)], 4100)
-    ctx = bb.bblock_create(6, 12, 10, "fp64")
+    ctx = bb.bblock_create(6, 12, 10, precision)
     rep = bb.bblock_autotune(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B, repeats=2)
     assert len(rep) == 4 and all(r["ms"] > 0 for r in rep)
     bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B)
