@@ -86,7 +86,11 @@ void bblock_destroy(bblock_ctx* ctx);
 const char* bblock_last_error(const bblock_ctx* ctx);
 
 /* Synchronise the stream of the last call and report device-side status:
- * BBLOCK_OK, BBLOCK_ERR_CUDA (a launch or kernel failed) or BBLOCK_ERR_DEVICE_FLAG. */
+ * BBLOCK_OK, BBLOCK_ERR_CUDA (a launch or kernel failed), BBLOCK_ERR_TIMEOUT (a bounded
+ * device wait gave up; the kernel stopped early and its blocks are invalid) or
+ * BBLOCK_ERR_DEVICE_FLAG (an inconsistent job table, or an index violation found by the
+ * checked kernel variant). The status word is cleared once reported, so the context stays
+ * usable for the next call. */
 int bblock_status(bblock_ctx* ctx);
 
 /* Baryon blocks of n_t time slices and one noise triple (Eq. 2 then Eq. 1).
@@ -151,6 +155,13 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 #define BBLOCK_OPT_CHECKS 5    /* 1: the tensor-core contraction checks every global index
                                   against its buffer, skips and records violations (reported
                                   by bblock_status); 0 (default): no checks */
+#define BBLOCK_OPT_WAIT_LIMIT_US 7  /* test hook: limit of the tensor-core contraction's
+                                       bounded waits in microseconds (0: the default of about
+                                       2 s); a wait that runs out sets the status word, which
+                                       bblock_status reports as BBLOCK_ERR_TIMEOUT */
+#define BBLOCK_OPT_FAIL_NEXT_ALLOC 8 /* test hook: 1 makes the next device allocation of the
+                                       context fail as if the device were out of memory
+                                       (BBLOCK_ERR_OOM), once */
 #define BBLOCK_OPT_WAVE_MB 6   /* workspace budget of one wave of jobs, MiB: a batch whose
                                   fields and partial blocks exceed it runs as several waves
                                   of launches; 0 (default): half the device memory free at

@@ -40,7 +40,8 @@ EXPORTED = (
     "bblock_costmodel_train", "bblock_costmodel_predict",
 )
 TUNE_FEATURES = 12
-OPTIONS = {"graphs": 1, "tc_nc": 2, "tc_chunk": 3, "slabs": 4, "checks": 5, "wave_mb": 6}
+OPTIONS = {"graphs": 1, "tc_nc": 2, "tc_chunk": 3, "slabs": 4, "checks": 5, "wave_mb": 6,
+           "wait_limit_us": 7, "fail_next_alloc": 8}
 
 
 class BblockError(RuntimeError):

@@ -63,6 +63,9 @@ struct bblock_ctx {
   size_t graph_tab_off = 0;
   size_t call_tab_bytes = 0;  // slots the last call's uploads took, summed over its waves
   size_t opt_wave_bytes = 0;  // workspace budget per wave set by the caller (0: default)
+  int opt_wait_us = 0;        // test hook: bounded-wait limit in microseconds (0: default)
+  int opt_fail_alloc = 0;     // test hook: the next device allocation fails once
+  long long cycles_per_us = 2070;
 };
 
 namespace {
@@ -144,6 +147,10 @@ void drop_graph(bblock_ctx* c) {
 int grow_device(bblock_ctx* c, char** p, size_t* cap, size_t need) {
   if (need <= *cap) return BBLOCK_OK;
   if (c->capturing) return fail(c, BBLOCK_ERR_UNSUPPORTED, "workspace growth during graph capture");
+  if (c->opt_fail_alloc) {
+    c->opt_fail_alloc = 0;
+    return fail(c, BBLOCK_ERR_OOM, "allocation of %zu bytes failed (forced by the test hook)", need);
+  }
   drop_graph(c);  // the graph holds the old addresses
   if (*p) {
     cudaError_t e = cudaStreamSynchronize(c->last_stream);
@@ -541,6 +548,8 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     prm.status = c->d_status;
     prm.checks = c->opt_checks;
     prm.dbg = c->d_dbg;
+    prm.wait_limit = c->opt_wait_us > 0 ? (long long)c->opt_wait_us * c->cycles_per_us
+                                        : 4000000000LL;
     const int grid = (int)std::min<long long>(unit, grid_cap);
     for (int set = 0; set < sp.n_coef_sets; ++set) {
       const TcJob* d_jobs = reinterpret_cast<const TcJob*>(c->d_tab + fbytes + jbytes * set);
@@ -1002,6 +1011,11 @@ int bblock_create(bblock_ctx** out, const bblock_config* cfg) {
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   c->ws_budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
+  int khz = 0;   // SM clock: converts the wait-limit test hook from microseconds to cycles
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, cfg->device) == cudaSuccess && khz > 0)
+    c->cycles_per_us = std::max(1, khz / 1000);
+  else
+    cudaGetLastError();
   *out = c;
   return BBLOCK_OK;
 }
@@ -1040,6 +1054,12 @@ int bblock_status(bblock_ctx* c) {
   if (st) {
     unsigned long long d[4] = {0, 0, 0, 0};
     if (cudaMemcpy(d, c->d_dbg, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) cudaGetLastError();
+    // reported once: clear the word and the index record so the next call starts clean
+    if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->d_dbg, 0, 4 * sizeof(unsigned long long)) != cudaSuccess)
+      cudaGetLastError();
+    if (st & kStatusTimeout)
+      return fail(c, BBLOCK_ERR_TIMEOUT, "a bounded device wait gave up (status word 0x%x)", st);
     return fail(c, BBLOCK_ERR_DEVICE_FLAG,
                 "device status word 0x%x (index check: site %llu job %llu index %llu bound %llu)",
                 st, d[0], d[1], d[2], d[3]);
@@ -1295,6 +1315,16 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       if (value < 0) break;
       c->opt_wave_bytes = (size_t)value << 20;
       return BBLOCK_OK;
+    case BBLOCK_OPT_WAIT_LIMIT_US:
+      if (value < 0) break;
+      c->opt_wait_us = value;
+      drop_graph(c);            // the limit is a kernel parameter captured in the graph
+      c->last_sig.clear();
+      return BBLOCK_OK;
+    case BBLOCK_OPT_FAIL_NEXT_ALLOC:
+      if (value != 0 && value != 1) break;
+      c->opt_fail_alloc = value;
+      return BBLOCK_OK;
     default:
       break;
   }
@@ -1309,6 +1339,8 @@ int bblock_get_option(const bblock_ctx* c, int option) {
     case BBLOCK_OPT_TC_CHUNK: return c->opt_tc_chunk;
     case BBLOCK_OPT_SLABS: return c->opt_slabs;
     case BBLOCK_OPT_WAVE_MB: return (int)(c->opt_wave_bytes >> 20);
+    case BBLOCK_OPT_WAIT_LIMIT_US: return c->opt_wait_us;
+    case BBLOCK_OPT_FAIL_NEXT_ALLOC: return c->opt_fail_alloc;
     case BBLOCK_OPT_CHECKS: return c->opt_checks;
     default: return BBLOCK_ERR_INVALID_ARG;
   }

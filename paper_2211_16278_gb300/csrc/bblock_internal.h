@@ -109,6 +109,8 @@ struct TcParams {
   // first violation is recorded in dbg[0..3] = (site code, job, index, bound) and skipped
   int checks;
   unsigned long long* dbg;
+  // limit of every bounded wait, in SM cycles (about 2 s by default; a test hook shortens it)
+  long long wait_limit;
 };
 
 enum TcForm { TC_BF16_3 = 0, TC_BF16_6 = 1, TC_BF16_9 = 2, TC_TF32_3 = 3 };

@@ -44,7 +44,7 @@ template <bool TF32> struct Roles {
   static constexpr int kThreads = kProdWarp0 * 32 + kProdThreads;
 };
 constexpr int kMaxNC = 48;
-constexpr long long kWaitCycles = 4000000000LL;  // about 2 s
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s: the default limit of every wait
 constexpr int kBarProd = 1, kBarEpi = 2;
 constexpr int kAPlaneBytes = kTcM * 96;          // 128 rows x 96 bytes of K per stage
 constexpr int kBPlaneBytes = kMaxNC * 96;
@@ -245,15 +245,19 @@ __device__ __forceinline__ Unit decode_unit(const TcParams& prm, long long u, in
   return w;
 }
 
-// Bounded wait by one thread; on timeout raise the CTA abort flag and the status bit.
+// Bounded wait by one thread: gives up after `limit` SM cycles, raising the CTA abort flag
+// and the status bit, or as soon as another role has raised the abort flag. With
+// abort_flag == nullptr only the time limit ends the wait (the MMA thread's final wait for
+// its own MMAs, which must complete before TMEM is freed even after an abort).
 __device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t parity,
-                                             volatile int* abort_flag, int* status) {
+                                             volatile int* abort_flag, int* status,
+                                             long long limit) {
   const long long t0 = clock64();
   while (true) {
     if (mbar_try(mbar, parity)) return true;
-    if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
-      *abort_flag = 1;
+    if (abort_flag && *abort_flag) return false;
+    if (clock64() - t0 > limit) {
+      if (abort_flag) *abort_flag = 1;
       atomicOr(status, kStatusTimeout);
       return false;
     }
@@ -370,7 +374,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
         bool ok = !abort_flag;
         if (ok && s_g >= STAGES)
           ok = wait_bounded(smem_u32(&bar_empty[slot]), (uint32_t)(((s_g / STAGES) + 1) & 1),
-                            &abort_flag, prm.status);
+                            &abort_flag, prm.status, prm.wait_limit);
         if (ok && row_used) {
           float re[3][8], im[3][8];
           // first group of this thread's run of 8
@@ -473,10 +477,10 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
                                   st == w.n_stages - 1;
           if (chunk_first && c_g >= 2) {
             if (!wait_bounded(smem_u32(&bar_acc_empty[buf]), (uint32_t)(((c_g >> 1) + 1) & 1),
-                              &abort_flag, prm.status)) { stop = true; break; }
+                              &abort_flag, prm.status, prm.wait_limit)) { stop = true; break; }
           }
           if (!wait_bounded(smem_u32(&bar_full[slot]), (uint32_t)((s_g / STAGES) & 1),
-                            &abort_flag, prm.status)) { stop = true; break; }
+                            &abort_flag, prm.status, prm.wait_limit)) { stop = true; break; }
           tc_fence_after();
           const uint32_t lead_r = tmem + (uint32_t)(buf * 4 * NC);
           const uint32_t lead_i = lead_r + NC, corr_r = lead_r + 2 * NC, corr_i = lead_r + 3 * NC;
@@ -508,8 +512,10 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
           }
         }
       }
+      // every MMA this thread issued must be complete before TMEM is freed, also after an
+      // abort: this wait ignores the abort flag and keeps the default limit
       tc_commit(smem_u32(&bar_final));
-      wait_bounded(smem_u32(&bar_final), 0u, &abort_flag, prm.status);
+      wait_bounded(smem_u32(&bar_final), 0u, nullptr, prm.status, kWaitCycles);
     }
     __syncwarp();
   } else {
@@ -527,7 +533,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
         bool ok = !abort_flag;
         if (ok)
           ok = wait_bounded(smem_u32(&bar_acc_full[buf]), (uint32_t)((c_g >> 1) & 1),
-                            &abort_flag, prm.status);
+                            &abort_flag, prm.status, prm.wait_limit);
         // the TMEM loads below are warp-collective: decide per warp
         ok = __all_sync(0xffffffffu, ok);
         if (ok) {
