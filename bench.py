@@ -74,6 +74,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU seconds of one oracle sample")
+    ap.add_argument("--no-triplet", action="store_true",
+                    help="skip the mode-triplet ordering's measurement")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the tensor-core forms (time the FP64 form only)")
     ap.add_argument("--form", choices=["fp64", "df64", "bf16x6", "bf16x9", "tf32x3", "bf16x3"],
@@ -191,6 +193,7 @@ def oracle_sample(inp, target_s: float):
         oracle.bblock_sampled(w.L, inp.V[t], *[inp.phi[0][i][t] for i in range(3)],
                               inp.momenta, inp.spins, inp.coeffs, d1s, d2s, all3)
 
+    run(0, list(range(n1)), [0])                 # warm-up (thread pool start)
     t0 = time.perf_counter()
     run(0, list(range(n1)), [0])                 # one d1 block x one d2 value
     t_unit = max(time.perf_counter() - t0, 1e-3)
@@ -475,6 +478,52 @@ def run_ours(args):
             }
             bb.bblock_destroy(c2)
 
+    # the mode-triplet ordering (Sec. 2, Eq. 4): T per time slice (noise-independent), then
+    # blocks from T by three FP64 mode products; the crossover is the number of noise
+    # triples per time slice above which T + n * (blocks from T) beats n * (direct blocks)
+    triplet = None
+    if not args.no_triplet and not batched and max(nd0 := inp.ndil[0]) <= w.n_ev <= 256:
+        triplet = {}
+        mom = inp.momenta
+        Tbuf = torch.empty((w.n_t, P, w.n_ev, w.n_ev, w.n_ev), dtype=torch.complex128, device=dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for name in ("fp64", "df64"):
+            c3 = bb.bblock_create(w.L, w.n_ev, w.n_ev, FORMS[name][0], device=local)
+            bb.bblock_mode_triplet(c3, V, mom, T_out=Tbuf, stream=stream)    # warm-up
+            bb.bblock_status(c3)
+            ev0.record(stream)
+            bb.bblock_mode_triplet(c3, V, mom, T_out=Tbuf, stream=stream)
+            ev1.record(stream)
+            bb.bblock_status(c3)
+            triplet[f"T_ms_per_time_slice_{name}"] = ev0.elapsed_time(ev1) / w.n_t
+            if name == "df64":
+                Bt = torch.empty_like(outs[0])
+                for k in range(max(1, args.warmup)):
+                    bb.bblock_from_triplet(c3, Tbuf, *phis[0], inp.spins, inp.coeffs, B_out=Bt,
+                                           stream=stream)
+                bb.bblock_status(c3)
+                ev0.record(stream)
+                for k in range(args.steps):
+                    bb.bblock_from_triplet(c3, Tbuf, *phis[0], inp.spins, inp.coeffs, B_out=Bt,
+                                           stream=stream)
+                ev1.record(stream)
+                bb.bblock_status(c3)
+                ft = ev0.elapsed_time(ev1) / args.steps / w.n_t
+                triplet["blocks_from_T_ms_per_time_slice"] = ft
+                triplet["rel_frobenius_err_vs_fp64_form"] = float(
+                    np.linalg.norm(Bt.cpu().numpy() - outs[0].cpu().numpy()) /
+                    np.linalg.norm(outs[0].cpu().numpy()))
+            bb.bblock_destroy(c3)
+        direct = {"fp64": ms / args.steps / w.n_t}
+        if "df64" in forms:
+            direct["df64"] = forms["df64"]["ms_per_step"] / w.n_t
+        triplet["direct_ms_per_time_slice"] = direct
+        ft = triplet["blocks_from_T_ms_per_time_slice"]
+        triplet["crossover_noise_triples"] = {
+            k: (triplet[f"T_ms_per_time_slice_{k}"] / (v - ft) if v > ft else None)
+            for k, v in direct.items()}
+        del Tbuf
+
     # end to end through the public API with host buffers: every step copies the inputs
     # from pinned host memory, computes, and copies the blocks back
     e2e = None
@@ -550,6 +599,7 @@ def run_ours(args):
             "e2e": e2e,
             "clocks": clk.summary(),
             "forms": forms,
+            "mode_triplet": triplet,
         }
         print(json.dumps(line), flush=True)
     bb.bblock_destroy(ctx)

@@ -137,6 +137,30 @@ int bblock_compute_batch(bblock_ctx* ctx, const bblock_job* jobs, int n_jobs,
                          const int32_t* momenta, int n_mom, const int32_t* spin_idx,
                          const double* spin_coeffs, int n_spin, int coeff_per_mom, void* stream);
 
+/* ---------------------------------------------------------------- mode-triplet ordering
+ * Eq. (3) can be evaluated in two steps through the eigenvector mode triplet of Eq. (4)
+ * (Sec. 2): T does not depend on the noise, dilution or spin, so one T per time slice
+ * serves every noise triple and spin operator of a run.
+ *
+ * bblock_mode_triplet: T[t][p][l1][l2][l3] = sum_x e^{-i p.x} eps_abc V[l1][x][a]
+ * V[l2][x][b] V[l3][x][c] for every time slice, computed by the context's form (it is the
+ * contraction with identity coefficients). V as in bblock_compute (device); T_out device,
+ * complex128 [n_t][n_mom][n_ev][n_ev][n_ev], l3 fastest, caller-owned. Requires
+ * max_ndil >= n_ev (BBLOCK_ERR_INVALID_ARG otherwise). Asynchronous on `stream`. */
+int bblock_mode_triplet(bblock_ctx* ctx, int n_t, const void* V, const int32_t* momenta,
+                        int n_mom, void* T_out, void* stream);
+
+/* bblock_from_triplet: B[t][p][d1][d2][d3] = sum_s c_s sum_{l1 l2 l3} T[t][p][l1][l2][l3]
+ * phi1[t][alpha_s n_ev + l1][d1] phi2[t][beta_s n_ev + l2][d2] phi3[t][gamma_s n_ev + l3][d3]
+ * as three batched complex mode products in FP64 (per time slice and (alpha, beta) pair:
+ * T x3 folded phi3, then x2 phi2, then x1 phi1). T as written by bblock_mode_triplet; phi_i,
+ * B_out, spins and coefficients as in bblock_compute (device buffers; the momenta
+ * themselves are not needed, only their number). Asynchronous on `stream`. */
+int bblock_from_triplet(bblock_ctx* ctx, int n_t, const void* T, const void* phi1,
+                        const void* phi2, const void* phi3, int nd1, int nd2, int nd3,
+                        int n_mom, const int32_t* spin_idx, const double* spin_coeffs,
+                        int n_spin, int coeff_per_mom, void* B_out, void* stream);
+
 /* Device bytes the context holds right now (workspace + caches). */
 size_t bblock_workspace_bytes(const bblock_ctx* ctx);
 

@@ -37,7 +37,8 @@ EXPORTED = (
     "bblock_contract_noalloc", "bblock_set_option", "bblock_get_option", "bblock_autotune",
     "bblock_costmodel_create", "bblock_costmodel_destroy", "bblock_costmodel_num_params",
     "bblock_costmodel_get_params", "bblock_costmodel_set_params", "bblock_costmodel_gradient",
-    "bblock_costmodel_train", "bblock_costmodel_predict",
+    "bblock_costmodel_train", "bblock_costmodel_predict", "bblock_mode_triplet",
+    "bblock_from_triplet",
 )
 TUNE_FEATURES = 12
 OPTIONS = {"graphs": 1, "tc_nc": 2, "tc_chunk": 3, "slabs": 4, "checks": 5, "wave_mb": 6,
@@ -100,6 +101,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bblock_compute_host.restype = I
     lib.bblock_compute_batch.argtypes = [P, ctypes.POINTER(bblock_job), I, P, I, P, P, I, I, P]
     lib.bblock_compute_batch.restype = I
+    lib.bblock_mode_triplet.argtypes = [P, I, P, P, I, P, P]
+    lib.bblock_mode_triplet.restype = I
+    lib.bblock_from_triplet.argtypes = [P, I, P, P, P, P, I, I, I, I, P, P, I, I, P, P]
+    lib.bblock_from_triplet.restype = I
     lib.bblock_workspace_bytes.argtypes = [P]
     lib.bblock_workspace_bytes.restype = ctypes.c_size_t
     lib.bblock_last_launch_count.argtypes = [P]
@@ -282,6 +287,51 @@ def bblock_compute(ctx: Context, V, phi1, phi2, phi3, momenta, spin_idx, spin_co
         ctx.handle, n_t, _dev_ptr(V, "V"), _dev_ptr(phi1, "phi1"), _dev_ptr(phi2, "phi2"),
         _dev_ptr(phi3, "phi3"), nds[0], nds[1], nds[2], mom.ctypes.data, mom.shape[0],
         spins.ctypes.data, coeffs.ctypes.data, spins.shape[0], per_mom, _dev_ptr(B_out, "B_out"),
+        _stream_handle(stream))
+    _check(ctx, rc)
+    return B_out
+
+
+def bblock_mode_triplet(ctx: Context, V, momenta, T_out=None, stream=None):
+    """Eq. (4): T[t][p][l1][l2][l3] of device eigenvectors V (n_t, n_ev, L^3, 3)."""
+    import torch
+    cfg = ctx.config
+    n_t = int(V.shape[0])
+    if tuple(V.shape) != (n_t, cfg.n_ev, cfg.L ** 3, 3):
+        raise ValueError("V must have shape (n_t, n_ev, L^3, 3)")
+    mom = np.ascontiguousarray(np.asarray(momenta, dtype=np.int32).reshape(-1, 3))
+    shape = (n_t, mom.shape[0], cfg.n_ev, cfg.n_ev, cfg.n_ev)
+    if T_out is None:
+        T_out = torch.empty(shape, dtype=torch.complex128, device=V.device)
+    elif tuple(T_out.shape) != shape:
+        raise ValueError(f"T_out must have shape {shape}")
+    rc = load().bblock_mode_triplet(ctx.handle, n_t, _dev_ptr(V, "V"), mom.ctypes.data,
+                                    mom.shape[0], _dev_ptr(T_out, "T_out"), _stream_handle(stream))
+    _check(ctx, rc)
+    return T_out
+
+
+def bblock_from_triplet(ctx: Context, T, phi1, phi2, phi3, spin_idx, spin_coeffs, B_out=None,
+                        stream=None):
+    """Blocks from the mode triplet (Eq. 3 in mode-triplet order); T as returned by
+    bblock_mode_triplet, phi_i (n_t, 4 n_ev, nd_i) device tensors."""
+    import torch
+    cfg = ctx.config
+    n_t, n_mom = int(T.shape[0]), int(T.shape[1])
+    if tuple(T.shape) != (n_t, n_mom, cfg.n_ev, cfg.n_ev, cfg.n_ev):
+        raise ValueError("T must have shape (n_t, n_mom, n_ev, n_ev, n_ev)")
+    nds = []
+    for i, p in enumerate((phi1, phi2, phi3)):
+        if p.ndim != 3 or p.shape[0] != n_t or p.shape[1] != 4 * cfg.n_ev:
+            raise ValueError(f"phi{i + 1} must have shape (n_t, 4*n_ev, nd)")
+        nds.append(int(p.shape[2]))
+    _, spins, coeffs, per_mom = _spin_arrays(np.zeros((n_mom, 3), np.int32), spin_idx, spin_coeffs)
+    if B_out is None:
+        B_out = torch.empty((n_t, n_mom, *nds), dtype=torch.complex128, device=T.device)
+    rc = load().bblock_from_triplet(
+        ctx.handle, n_t, _dev_ptr(T, "T"), _dev_ptr(phi1, "phi1"), _dev_ptr(phi2, "phi2"),
+        _dev_ptr(phi3, "phi3"), nds[0], nds[1], nds[2], n_mom, spins.ctypes.data,
+        coeffs.ctypes.data, spins.shape[0], per_mom, _dev_ptr(B_out, "B_out"),
         _stream_handle(stream))
     _check(ctx, rc)
     return B_out

@@ -40,6 +40,11 @@ struct bblock_ctx {
   // device staging for bblock_compute_host
   char* d_io = nullptr;
   size_t io_cap = 0;
+  // mode-triplet ordering: identity coefficients [4 n_ev][n_ev] and the mode-product
+  // intermediates (folded phi3, T x3 phi3', then x2 phi2)
+  double2* d_ident = nullptr;
+  char* d_tri = nullptr;
+  size_t tri_cap = 0;
   int last_launches = 0;
   size_t ws_budget = 0;
   // launch timing (bblock_profile_enable)
@@ -1031,6 +1036,8 @@ void bblock_destroy(bblock_ctx* c) {
   cudaFree(c->d_ws);
   cudaFree(c->d_tab);
   cudaFree(c->d_io);
+  cudaFree(c->d_ident);
+  cudaFree(c->d_tri);
   if (c->h_tab) cudaFreeHost(c->h_tab);
   if (c->tab_free) cudaEventDestroy(c->tab_free);
   drop_graph(c);
@@ -1127,6 +1134,145 @@ int bblock_compute_batch(bblock_ctx* c, const bblock_job* jobs_in, int n_jobs,
   });
   return run_jobs_cached(c, jobs, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom,
                   static_cast<cudaStream_t>(stream));
+}
+
+// Eq. (4): T[t][p] is the contraction with q_i = V, i.e. identity coefficients and the
+// single spin triple (0, 0, 0), computed by the context's form for every time slice.
+int bblock_mode_triplet(bblock_ctx* c, int n_t, const void* V, const int32_t* momenta, int n_mom,
+                        void* T_out, void* stream) {
+  if (!c) return BBLOCK_ERR_INVALID_ARG;
+  c->err.clear();
+  const int n_ev = c->cfg.n_ev;
+  if (n_t < 0) return fail(c, BBLOCK_ERR_INVALID_ARG, "n_t = %d < 0", n_t);
+  if (n_ev > c->cfg.max_ndil)
+    return fail(c, BBLOCK_ERR_INVALID_ARG, "the mode triplet needs max_ndil >= n_ev (%d)", n_ev);
+  const int32_t spin[3] = {0, 0, 0};
+  const double one[2] = {1.0, 0.0};
+  int rc = validate_common(c, momenta, n_mom, spin, one, 1, 0);
+  if (rc) return rc;
+  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; return BBLOCK_OK; }
+  CK(c, cudaSetDevice(c->cfg.device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!c->d_ident) {
+    if (c->capturing) return fail(c, BBLOCK_ERR_UNSUPPORTED, "allocation during graph capture");
+    if (cudaMalloc(&c->d_ident, sizeof(double2) * 4 * (size_t)n_ev * n_ev) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_ident = nullptr;
+      return fail(c, BBLOCK_ERR_OOM, "identity coefficients");
+    }
+    CK(c, launch_fill_identity(c->d_ident, n_ev, s));
+  }
+  const size_t vstride = (size_t)n_ev * c->rows;
+  const size_t tstride = (size_t)n_mom * n_ev * n_ev * n_ev;
+  std::vector<JobIn> jobs(n_t);
+  for (int t = 0; t < n_t; ++t) {
+    JobIn& j = jobs[t];
+    j.V = static_cast<const double2*>(V) + t * vstride;
+    j.phi[0] = j.phi[1] = j.phi[2] = c->d_ident;
+    j.nd[0] = j.nd[1] = j.nd[2] = n_ev;
+    j.B = static_cast<double2*>(T_out) + t * tstride;
+    rc = validate_job(c, j, t, true, n_mom);
+    if (rc) return rc;
+  }
+  return run_jobs_cached(c, jobs, momenta, n_mom, spin, one, 1, 0, s);
+}
+
+// Eq. (3) through the mode triplet: for every time slice and (alpha, beta) pair,
+//   U1 = T x3 phi3'   (phi3' = the pair's folded line-3 coefficients),
+//   U2 = U1 x2 phi2[beta],  B += U2 x1 phi1[alpha],
+// three batched complex GEMMs in FP64.
+int bblock_from_triplet(bblock_ctx* c, int n_t, const void* T, const void* phi1, const void* phi2,
+                        const void* phi3, int nd1, int nd2, int nd3, int n_mom,
+                        const int32_t* spin_idx, const double* spin_coeffs, int n_spin,
+                        int coeff_per_mom, void* B_out, void* stream) {
+  if (!c) return BBLOCK_ERR_INVALID_ARG;
+  c->err.clear();
+  const int n_ev = c->cfg.n_ev;
+  if (n_t < 0) return fail(c, BBLOCK_ERR_INVALID_ARG, "n_t = %d < 0", n_t);
+  // momenta are not needed (T already carries them); any valid array satisfies the check
+  std::vector<int32_t> mom_dummy(3 * (size_t)std::max(n_mom, 1), 0);
+  int rc = validate_common(c, mom_dummy.data(), n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom);
+  if (rc) return rc;
+  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; return BBLOCK_OK; }
+  const int nds[3] = {nd1, nd2, nd3};
+  for (int i = 0; i < 3; ++i)
+    if (nds[i] < 1 || nds[i] > c->cfg.max_ndil)
+      return fail(c, BBLOCK_ERR_INVALID_ARG, "nd%d = %d outside 1..max_ndil", i + 1, nds[i]);
+  const size_t tstride = (size_t)n_mom * n_ev * n_ev * n_ev;
+  const size_t pst[3] = {(size_t)4 * n_ev * nd1, (size_t)4 * n_ev * nd2, (size_t)4 * n_ev * nd3};
+  const size_t bstride = (size_t)n_mom * nd1 * nd2 * nd3;
+  const void* ptrs[5] = {T, phi1, phi2, phi3, B_out};
+  const size_t ext[5] = {tstride * n_t, pst[0] * n_t, pst[1] * n_t, pst[2] * n_t, bstride * n_t};
+  const char* names[5] = {"T", "phi1", "phi2", "phi3", "B_out"};
+  for (int k = 0; k < 5; ++k) {
+    if (!ptrs[k] || !aligned16(ptrs[k]) || !is_device_ptr(c, ptrs[k]))
+      return fail(c, BBLOCK_ERR_INVALID_ARG, "%s must be 16-byte aligned device memory", names[k]);
+    if (!within_allocation(ptrs[k], ext[k] * sizeof(double2)))
+      return fail(c, BBLOCK_ERR_INVALID_ARG, "%s extends past its allocation", names[k]);
+  }
+  SpinPlan sp;
+  rc = plan_spins(c, spin_idx, spin_coeffs, n_spin, coeff_per_mom, n_mom, &sp);
+  if (rc) return rc;
+  CK(c, cudaSetDevice(c->cfg.device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  // intermediates for the momenta of one coefficient set
+  const int P_set = coeff_per_mom ? 1 : n_mom;
+  const size_t f_bytes = align_up(sizeof(double2) * (size_t)n_ev * nd3, 256);
+  const size_t u1_bytes = align_up(sizeof(double2) * (size_t)P_set * n_ev * n_ev * nd3, 256);
+  const size_t u2_bytes = align_up(sizeof(double2) * (size_t)P_set * n_ev * nd2 * nd3, 256);
+  rc = grow_device(c, &c->d_tri, &c->tri_cap, f_bytes + u1_bytes + u2_bytes);
+  if (rc) return rc;
+  double2* fold = reinterpret_cast<double2*>(c->d_tri);
+  double2* U1 = reinterpret_cast<double2*>(c->d_tri + f_bytes);
+  double2* U2 = reinterpret_cast<double2*>(c->d_tri + f_bytes + u1_bytes);
+  int launches = 0;
+  const double2 one = make_double2(1.0, 0.0);
+  for (int t = 0; t < n_t; ++t) {
+    const double2* Tt = static_cast<const double2*>(T) + t * tstride;
+    const double2* p1 = static_cast<const double2*>(phi1) + t * pst[0];
+    const double2* p2 = static_cast<const double2*>(phi2) + t * pst[1];
+    const double2* p3 = static_cast<const double2*>(phi3) + t * pst[2];
+    double2* Bt = static_cast<double2*>(B_out) + t * bstride;
+    for (int set = 0; set < sp.n_coef_sets; ++set) {
+      const int p0 = coeff_per_mom ? set : 0;
+      for (int pr = 0; pr < sp.n_pairs; ++pr) {
+        FoldTerms ft{};
+        const auto& tl = sp.terms[set][pr];
+        ft.n = (int)tl.size();
+        for (int k = 0; k < ft.n; ++k) { ft.row[k] = tl[k].first; ft.w[k] = tl[k].second; }
+        CK(c, launch_fold_phi(p3, n_ev, nd3, ft, fold, s));
+        // U1[(p, l1, l2)][d3] = sum_l3 T[p][l1][l2][l3] phi3'[l3][d3]
+        ZgemmParams g{};
+        g.M = P_set * n_ev * n_ev; g.N = nd3; g.K = n_ev; g.batch = 1;
+        g.A = Tt + (size_t)p0 * n_ev * n_ev * n_ev; g.a_m = n_ev; g.a_k = 1;
+        g.B = fold; g.b_k = nd3; g.b_n = 1;
+        g.C = U1; g.c_m = nd3; g.c_n = 1;
+        g.alpha = one; g.accumulate = 0;
+        CK(c, launch_zgemm(g, s));
+        // U2[(p, l1)][d2][d3] = sum_l2 phi2[beta n_ev + l2][d2] U1[(p, l1, l2)][d3]
+        g = ZgemmParams{};
+        g.M = nd2; g.N = nd3; g.K = n_ev; g.batch = (long long)P_set * n_ev;
+        g.A = p2 + (size_t)sp.pair_beta[pr] * n_ev * nd2; g.a_m = 1; g.a_k = nd2; g.a_b = 0;
+        g.B = U1; g.b_k = nd3; g.b_n = 1; g.b_b = (long long)n_ev * nd3;
+        g.C = U2; g.c_m = nd3; g.c_n = 1; g.c_b = (long long)nd2 * nd3;
+        g.alpha = one; g.accumulate = 0;
+        CK(c, launch_zgemm(g, s));
+        // B[p][d1][(d2, d3)] (+)= sum_l1 phi1[alpha n_ev + l1][d1] U2[(p, l1)][(d2, d3)]
+        g = ZgemmParams{};
+        g.M = nd1; g.N = nd2 * nd3; g.K = n_ev; g.batch = P_set;
+        g.A = p1 + (size_t)sp.pair_alpha[pr] * n_ev * nd1; g.a_m = 1; g.a_k = nd1; g.a_b = 0;
+        g.B = U2; g.b_k = (long long)nd2 * nd3; g.b_n = 1; g.b_b = (long long)n_ev * nd2 * nd3;
+        g.C = Bt + (size_t)p0 * nd1 * nd2 * nd3; g.c_m = (long long)nd2 * nd3; g.c_n = 1;
+        g.c_b = (long long)nd1 * nd2 * nd3;
+        g.alpha = one; g.accumulate = pr > 0;
+        CK(c, launch_zgemm(g, s));
+        launches += 4;
+      }
+    }
+  }
+  c->last_launches = launches;
+  return BBLOCK_OK;
 }
 
 int bblock_compute_host(bblock_ctx* c, int n_t, const void* V, const void* phi1, const void* phi2,

@@ -124,6 +124,36 @@ cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab,
                                     long long max_elems, int checks, unsigned long long* dbg,
                                     int* status, cudaStream_t s);
 
+// ---------------------------------------------------------------- mode-triplet ordering
+
+// Line-3 coefficients of one (alpha, beta) pair: phi3' = sum_t w[t] phi3[row[t] N_ev + l][d].
+struct FoldTerms {
+  int n;
+  int row[kMaxTerms];
+  double2 w[kMaxTerms];
+};
+
+// Batched complex GEMM, FP64: for b < batch,
+//   C_b[m][n] = alpha * sum_k A_b[m][k] B_b[k][n]  (+ C_b[m][n] if accumulate),
+// element (m, k) of A_b at A + b * a_b + m * a_m + k * a_k (strides in elements), likewise B, C.
+struct ZgemmParams {
+  int M, N, K;
+  long long batch;
+  const double2* A;
+  long long a_m, a_k, a_b;
+  const double2* B;
+  long long b_k, b_n, b_b;
+  double2* C;
+  long long c_m, c_n, c_b;
+  double2 alpha;
+  int accumulate;
+};
+
+cudaError_t launch_fill_identity(double2* id, int n_ev, cudaStream_t s);
+cudaError_t launch_fold_phi(const double2* phi, int n_ev, int nd, const FoldTerms& terms,
+                            double2* out, cudaStream_t s);
+cudaError_t launch_zgemm(const ZgemmParams& p, cudaStream_t s);
+
 cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, cudaStream_t s);
 cudaError_t launch_project_fp64(const ProjField* d_fields, int n_fields, int rows, int n_ev,
                                 int max_nd, cudaStream_t s);
