@@ -177,8 +177,12 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 #define BBLOCK_OPT_TC_CHUNK 3  /* tensor-core forms: stages between accumulator drains, 1..8 */
 #define BBLOCK_OPT_SLABS 4     /* site slabs per job (split of the site sum), 1..4096 */
 #define BBLOCK_OPT_CHECKS 5    /* 1: the tensor-core contraction checks every global index
-                                  against its buffer, skips and records violations (reported
-                                  by bblock_status); 0 (default): no checks */
+                                  against its buffer, skips and records violations, and in
+                                  every form a 256-byte canary follows each workspace block
+                                  (fields, converted inputs, partial blocks), filled before
+                                  and verified after each wave; violations and overwritten
+                                  canaries are reported by bblock_status
+                                  (BBLOCK_ERR_DEVICE_FLAG); 0 (default): no checks */
 #define BBLOCK_OPT_WAIT_LIMIT_US 7  /* test hook: limit of the tensor-core contraction's
                                        bounded waits in microseconds (0: the default of about
                                        2 s); a wait that runs out sets the status word, which
@@ -186,6 +190,9 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 #define BBLOCK_OPT_FAIL_NEXT_ALLOC 8 /* test hook: 1 makes the next device allocation of the
                                        context fail as if the device were out of memory
                                        (BBLOCK_ERR_OOM), once */
+#define BBLOCK_OPT_CORRUPT_CANARY 9  /* test hook (with BBLOCK_OPT_CHECKS): 1 makes the next
+                                       call overwrite its first canary from the host, in
+                                       stream order between the fill and the check, once */
 #define BBLOCK_OPT_WAVE_MB 6   /* workspace budget of one wave of jobs, MiB: a batch whose
                                   fields and partial blocks exceed it runs as several waves
                                   of launches; 0 (default): half the device memory free at

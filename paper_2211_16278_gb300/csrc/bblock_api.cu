@@ -70,12 +70,14 @@ struct bblock_ctx {
   size_t opt_wave_bytes = 0;  // workspace budget per wave set by the caller (0: default)
   int opt_wait_us = 0;        // test hook: bounded-wait limit in microseconds (0: default)
   int opt_fail_alloc = 0;     // test hook: the next device allocation fails once
+  int opt_corrupt_canary = 0; // test hook: the next call overwrites its first canary once
   long long cycles_per_us = 2070;
 };
 
 namespace {
-enum KernelKind { K_PHASE = 0, K_PROJECT, K_CONTRACT, K_REDUCE, K_CONVERT, K_COUNT };
-const char* const kKernelNames[K_COUNT] = {"phase", "project", "contract", "reduce", "convert"};
+enum KernelKind { K_PHASE = 0, K_PROJECT, K_CONTRACT, K_REDUCE, K_CONVERT, K_CANARY, K_COUNT };
+const char* const kKernelNames[K_COUNT] = {"phase", "project", "contract", "reduce", "convert",
+                                           "canary"};
 
 cudaEvent_t take_event(bblock_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -422,10 +424,12 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
   const int min_slabs = (int)std::min<long long>(
       X, ((long long)X * sp.n_pairs + max_groups_per_unit - 1) / max_groups_per_unit);
   const int max_slabs = std::max(64, min_slabs);
+  // checks option: a canary after every field and partial block of a job
+  const size_t canary_bytes = c->opt_checks ? (size_t)(sp.n1 + sp.n2 + n3_fields + 1) * kCanaryBytes : 0;
   auto job_bytes = [&](const JobIn& j, int n_slab) {
     size_t f = (size_t)rows * (sp.n1 * j.nd[0] + sp.n2 * j.nd[1] + n3_fields * j.nd[2]) * sizeof(float2);
     size_t p = (size_t)n_slab * P_launch * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(float2);
-    return align_up(f, 256) + align_up(p, 256);
+    return align_up(f, 256) + align_up(p, 256) + canary_bytes;
   };
   size_t job_idx = 0;
   int rc;
@@ -458,11 +462,17 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
 
     std::vector<ProjFieldF> fields;
     std::vector<std::vector<TcJob>> tjobs(sp.n_coef_sets, std::vector<TcJob>(nj));
+    std::vector<uint32_t*> canaries;
     char* ws = c->d_ws;
     long long unit = 0;
     for (int k = 0; k < nj; ++k) {
       const JobIn& j = jobs[job_idx + k];
       char* base = ws;
+      auto canary = [&](char*& at) {
+        if (!c->opt_checks) return;
+        canaries.push_back(reinterpret_cast<uint32_t*>(at));
+        at += kCanaryBytes;
+      };
       auto add_field = [&](const double2* phi, int nd, int n_terms, const int* offs,
                            const double2* w) -> float2* {
         ProjFieldF f{};
@@ -473,6 +483,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
         f.n_terms = n_terms;
         for (int t = 0; t < n_terms; ++t) { f.row_off[t] = offs[t]; f.w[t] = w[t]; }
         base += (size_t)rows * nd * sizeof(float2);
+        canary(base);
         fields.push_back(f);
         return f.q;
       };
@@ -500,6 +511,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       base = c->d_ws + align_up((size_t)(base - c->d_ws), 256);
       float2* partial = reinterpret_cast<float2*>(base);
       base += align_up((size_t)n_slab * P_launch * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(float2), 256);
+      canary(base);
       ws = base;
       const int m_tiles = (j.nd[0] * j.nd[1] + 127) / 128;           // (d1, d2) pairs
       const int n_tiles = (P_launch * j.nd[2] + NC - 1) / NC;        // (p, d3) columns
@@ -526,15 +538,30 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       if (!within_workspace(c, tj.partial, (size_t)n_slab * P_launch * tj.nd1 * tj.nd2 * tj.nd3 * sizeof(float2)))
         return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: partial block outside the workspace");
     }
+    for (uint32_t* cn : canaries)
+      if (!within_workspace(c, cn, kCanaryBytes))
+        return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: canary outside the workspace");
     const size_t fbytes = align_up(fields.size() * sizeof(ProjFieldF), 256);
     const size_t jbytes = align_up((size_t)nj * sizeof(TcJob), 256);
-    std::vector<char> tab(fbytes + jbytes * sp.n_coef_sets);
+    const size_t cofs = fbytes + jbytes * sp.n_coef_sets;
+    std::vector<char> tab(cofs + canaries.size() * sizeof(uint32_t*));
     memcpy(tab.data(), fields.data(), fields.size() * sizeof(ProjFieldF));
     for (int set = 0; set < sp.n_coef_sets; ++set)
       memcpy(tab.data() + fbytes + jbytes * set, tjobs[set].data(), (size_t)nj * sizeof(TcJob));
+    if (!canaries.empty()) memcpy(tab.data() + cofs, canaries.data(), canaries.size() * sizeof(uint32_t*));
     rc = upload_tables(c, tab.data(), tab.size(), s);
     if (rc) return rc;
     const ProjFieldF* d_fields = reinterpret_cast<const ProjFieldF*>(c->d_tab);
+    uint32_t* const* d_canaries = reinterpret_cast<uint32_t* const*>(c->d_tab + cofs);
+    if (!canaries.empty()) {
+      CK(c, timed_launch(c, K_CANARY, s, [&] {
+        return launch_canaries(d_canaries, (int)canaries.size(), false, c->d_status, s);
+      }));
+      if (c->opt_corrupt_canary && !c->capturing) {   // test hook: a simulated overrun
+        c->opt_corrupt_canary = 0;
+        CK(c, cudaMemsetAsync(canaries[0], 0x5a, 4, s));
+      }
+    }
     CK(c, timed_launch(c, K_PROJECT, s, [&] {
       return launch_project_f32(d_fields, (int)fields.size(), rows, n_ev, max_ndf, c->opt_checks,
                                 c->d_dbg, c->d_status, s);
@@ -566,6 +593,10 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
                                        c->d_dbg, c->d_status, s);
       }));
     }
+    if (!canaries.empty())
+      CK(c, timed_launch(c, K_CANARY, s, [&] {
+        return launch_canaries(d_canaries, (int)canaries.size(), true, c->d_status, s);
+      }));
     job_idx = end;
   }
   return BBLOCK_OK;
@@ -603,11 +634,14 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
     return align_up((size_t)rows * n_ev * sizeof(float4), 256) +
            align_up((size_t)4 * n_ev * (j.nd[0] + j.nd[1] + j.nd[2]) * sizeof(float4), 256);
   };
+  // checks option: a canary after every field, the partial block and the converted inputs
+  const size_t canary_bytes =
+      c->opt_checks ? (size_t)(sp.n1 + sp.n2 + n3_fields + 1 + (df ? 1 : 0)) * kCanaryBytes : 0;
   // bytes per job: fields + partials at the largest slab count (+ double-float inputs)
   auto job_bytes = [&](const JobIn& j, int n_slab) {
     size_t f = (size_t)rows * (sp.n1 * j.nd[0] + sp.n2 * j.nd[1] + n3_fields * j.nd[2]) * sizeof(double2);
     size_t p = (size_t)n_slab * n_mom * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(double2);
-    return align_up(f, 256) + align_up(p, 256) + df_in_bytes(j);
+    return align_up(f, 256) + align_up(p, 256) + df_in_bytes(j) + canary_bytes;
   };
 
   size_t job_idx = 0;
@@ -647,12 +681,18 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
     std::vector<ProjField> fields;
     std::vector<std::vector<ContractJob>> cjobs(sp.n_coef_sets, std::vector<ContractJob>(nj));
     std::vector<DfConvSeg> segs;
+    std::vector<uint32_t*> canaries;
     long long max_seg = 0;
     char* ws = c->d_ws;
     long long unit = 0;
     for (int k = 0; k < nj; ++k) {
       const JobIn& j = jobs[job_idx + k];
       char* base = ws;
+      auto canary = [&](char*& at) {
+        if (!c->opt_checks) return;
+        canaries.push_back(reinterpret_cast<uint32_t*>(at));
+        at += kCanaryBytes;
+      };
       // double-float form: the job's inputs are converted to float4 planes first
       const double2* Vin = j.V;
       const double2* phin[3] = {j.phi[0], j.phi[1], j.phi[2]};
@@ -674,6 +714,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
           phi_base += (size_t)4 * n_ev * j.nd[i] * sizeof(float4);
         }
         base += df_in_bytes(j);
+        canary(base);
       }
       auto add_field = [&](const double2* phi, int nd, int n_terms, const int* offs,
                            const double2* w) -> double2* {
@@ -685,6 +726,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
         f.n_terms = n_terms;
         for (int t = 0; t < n_terms; ++t) { f.row_off[t] = offs[t]; f.w[t] = w[t]; }
         base += (size_t)rows * nd * sizeof(double2);
+        canary(base);
         fields.push_back(f);
         return f.q;
       };
@@ -712,6 +754,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       base = c->d_ws + align_up((size_t)(base - c->d_ws), 256);
       double2* partial = reinterpret_cast<double2*>(base);
       base += align_up((size_t)n_slab * n_mom * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(double2), 256);
+      canary(base);
       ws = base;
       const int m_tiles = (j.nd[0] * j.nd[1] + 16 * tl.rm - 1) / (16 * tl.rm);
       const int n_tiles = (j.nd[2] + 16 * tl.rn - 1) / (16 * tl.rn);
@@ -740,17 +783,32 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
     for (const DfConvSeg& g : segs)
       if (!within_workspace(c, g.dst, (size_t)g.n * sizeof(float4)))
         return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: converted input outside the workspace");
+    for (uint32_t* cn : canaries)
+      if (!within_workspace(c, cn, kCanaryBytes))
+        return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: canary outside the workspace");
     const size_t fbytes = align_up(fields.size() * sizeof(ProjField), 256);
     const size_t jbytes = align_up((size_t)nj * sizeof(ContractJob), 256);
     const size_t sofs = fbytes + jbytes * sp.n_coef_sets;
-    std::vector<char> tab(sofs + segs.size() * sizeof(DfConvSeg));
+    const size_t cofs = sofs + align_up(segs.size() * sizeof(DfConvSeg), 256);
+    std::vector<char> tab(cofs + canaries.size() * sizeof(uint32_t*));
     memcpy(tab.data(), fields.data(), fields.size() * sizeof(ProjField));
     for (int set = 0; set < sp.n_coef_sets; ++set)
       memcpy(tab.data() + fbytes + jbytes * set, cjobs[set].data(), (size_t)nj * sizeof(ContractJob));
     if (!segs.empty()) memcpy(tab.data() + sofs, segs.data(), segs.size() * sizeof(DfConvSeg));
+    if (!canaries.empty()) memcpy(tab.data() + cofs, canaries.data(), canaries.size() * sizeof(uint32_t*));
     rc = upload_tables(c, tab.data(), tab.size(), s);
     if (rc) return rc;
     const ProjField* d_fields = reinterpret_cast<const ProjField*>(c->d_tab);
+    uint32_t* const* d_canaries = reinterpret_cast<uint32_t* const*>(c->d_tab + cofs);
+    if (!canaries.empty()) {
+      CK(c, timed_launch(c, K_CANARY, s, [&] {
+        return launch_canaries(d_canaries, (int)canaries.size(), false, c->d_status, s);
+      }));
+      if (c->opt_corrupt_canary && !c->capturing) {   // test hook: a simulated overrun
+        c->opt_corrupt_canary = 0;
+        CK(c, cudaMemsetAsync(canaries[0], 0x5a, 4, s));
+      }
+    }
 
     if (df) {
       CK(c, timed_launch(c, K_CONVERT, s, [&] {
@@ -797,6 +855,10 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       return launch_reduce_slabs(reinterpret_cast<const ContractJob*>(c->d_tab + fbytes), nj,
                                  n_slab, n_mom, max_elems, s);
     }));
+    if (!canaries.empty())
+      CK(c, timed_launch(c, K_CANARY, s, [&] {
+        return launch_canaries(d_canaries, (int)canaries.size(), true, c->d_status, s);
+      }));
     job_idx = end;
   }
   return BBLOCK_OK;
@@ -1067,6 +1129,9 @@ int bblock_status(bblock_ctx* c) {
       cudaGetLastError();
     if (st & kStatusTimeout)
       return fail(c, BBLOCK_ERR_TIMEOUT, "a bounded device wait gave up (status word 0x%x)", st);
+    if (st & kStatusCanary)
+      return fail(c, BBLOCK_ERR_DEVICE_FLAG,
+                  "a workspace canary was overwritten: a kernel wrote past its block (status word 0x%x)", st);
     return fail(c, BBLOCK_ERR_DEVICE_FLAG,
                 "device status word 0x%x (index check: site %llu job %llu index %llu bound %llu)",
                 st, d[0], d[1], d[2], d[3]);
@@ -1471,6 +1536,12 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       if (value != 0 && value != 1) break;
       c->opt_fail_alloc = value;
       return BBLOCK_OK;
+    case BBLOCK_OPT_CORRUPT_CANARY:
+      if (value != 0 && value != 1) break;
+      c->opt_corrupt_canary = value;
+      drop_graph(c);            // the hook acts on plain launches only
+      c->last_sig.clear();
+      return BBLOCK_OK;
     default:
       break;
   }
@@ -1487,6 +1558,7 @@ int bblock_get_option(const bblock_ctx* c, int option) {
     case BBLOCK_OPT_WAVE_MB: return (int)(c->opt_wave_bytes >> 20);
     case BBLOCK_OPT_WAIT_LIMIT_US: return c->opt_wait_us;
     case BBLOCK_OPT_FAIL_NEXT_ALLOC: return c->opt_fail_alloc;
+    case BBLOCK_OPT_CORRUPT_CANARY: return c->opt_corrupt_canary;
     case BBLOCK_OPT_CHECKS: return c->opt_checks;
     default: return BBLOCK_ERR_INVALID_ARG;
   }

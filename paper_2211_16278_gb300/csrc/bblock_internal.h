@@ -15,6 +15,8 @@ constexpr int kThreads = 256;   // threads per CTA of the FP64 kernels
 constexpr int kStatusBadJob = 1;
 constexpr int kStatusTimeout = 2;   // a bounded wait of the tensor-core kernel gave up
 constexpr int kStatusBadIndex = 4;  // a checked kernel found an index outside its buffer
+constexpr int kStatusCanary = 8;    // a workspace canary was overwritten (checks option)
+constexpr int kCanaryBytes = 256;   // canary after every workspace block (checks option)
 
 // One reconstructed field of Eq. (2):
 //   q[r][d] = sum_l V[l][r] * Phi[l][d],   Phi[l][d] = sum_t w[t] * phi[row_off[t] + l][d],
@@ -153,6 +155,10 @@ cudaError_t launch_fill_identity(double2* id, int n_ev, cudaStream_t s);
 cudaError_t launch_fold_phi(const double2* phi, int n_ev, int nd, const FoldTerms& terms,
                             double2* out, cudaStream_t s);
 cudaError_t launch_zgemm(const ZgemmParams& p, cudaStream_t s);
+
+// Fill (check == false) or verify (check == true) the n canaries listed at d_list.
+cudaError_t launch_canaries(uint32_t* const* d_list, int n, bool check, int* status,
+                            cudaStream_t s);
 
 cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, cudaStream_t s);
 cudaError_t launch_project_fp64(const ProjField* d_fields, int n_fields, int rows, int n_ev,

@@ -9,6 +9,10 @@
   BBLOCK_ERR_OOM and the context recovers on the next call.
 * Invalid sizes: a line with no (or negative, or too many) dilution columns is rejected
   before any launch.
+* Workspace canaries (checks option): in every form the canaries after the fields, the
+  converted inputs and the partial blocks stay intact. A test hook overwrites one from the
+  host, in stream order and inside the library's own workspace, so no kernel misbehaves;
+  the check kernel must report it, and the context must then compute correct blocks.
 """
 import numpy as np
 import pytest
@@ -94,4 +98,39 @@ def test_a_line_without_dilution_columns_is_rejected(env):
     B = bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs)
     bb.bblock_status(ctx)
     assert rel(B.cpu().numpy(), ref) <= 1e-12
+    bb.bblock_destroy(ctx)
+
+
+FORMS = [("fp64", 6, 1e-12), ("df64", 6, 1e-12), ("bf16", 6, 1e-6), ("tf32x3", 6, 1e-6),
+         ("bf16", 3, 1e-4)]
+
+
+@pytest.mark.parametrize("form", range(len(FORMS)))
+def test_workspace_canaries_stay_intact(env, form):
+    torch, bb = env
+    precision, products, tol = FORMS[form]
+    inp, V, phis, ref = _case(torch)
+    ctx = bb.bblock_create(6, 16, 16, precision, bf16_products=products)
+    bb.bblock_set_option(ctx, "checks", 1)
+    B = bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs)
+    bb.bblock_status(ctx)
+    assert rel(B.cpu().numpy(), ref) <= tol
+    assert bb.bblock_last_launch_count(ctx) >= 2          # fill and check launches included
+    bb.bblock_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_an_overwritten_canary_is_reported(env, precision):
+    torch, bb = env
+    inp, V, phis, ref = _case(torch)
+    ctx = bb.bblock_create(6, 16, 16, precision)
+    bb.bblock_set_option(ctx, "checks", 1)
+    bb.bblock_set_option(ctx, "corrupt_canary", 1)
+    bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs)
+    with pytest.raises(bb.BblockError, match="DEVICE_FLAG"):
+        bb.bblock_status(ctx)
+    assert "canary" in bb.bblock_last_error(ctx)
+    B = bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs)
+    bb.bblock_status(ctx)
+    assert rel(B.cpu().numpy(), ref) <= (1e-12 if precision == "fp64" else 1e-6)
     bb.bblock_destroy(ctx)
