@@ -424,12 +424,17 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
   const int min_slabs = (int)std::min<long long>(
       X, ((long long)X * sp.n_pairs + max_groups_per_unit - 1) / max_groups_per_unit);
   const int max_slabs = std::max(64, min_slabs);
-  // checks option: a canary after every field and partial block of a job
-  const size_t canary_bytes = c->opt_checks ? (size_t)(sp.n1 + sp.n2 + n3_fields + 1) * kCanaryBytes : 0;
+  // checks option: a canary after the converted inputs and every field and partial block
+  const size_t canary_bytes = c->opt_checks ? (size_t)(sp.n1 + sp.n2 + n3_fields + 2) * kCanaryBytes : 0;
+  // FP32 copies of a job's inputs (V and the three phi_i), converted once per call
+  auto in_bytes = [&](const JobIn& j) -> size_t {
+    return align_up((size_t)rows * n_ev * sizeof(float2), 256) +
+           align_up((size_t)4 * n_ev * (j.nd[0] + j.nd[1] + j.nd[2]) * sizeof(float2), 256);
+  };
   auto job_bytes = [&](const JobIn& j, int n_slab) {
     size_t f = (size_t)rows * (sp.n1 * j.nd[0] + sp.n2 * j.nd[1] + n3_fields * j.nd[2]) * sizeof(float2);
     size_t p = (size_t)n_slab * P_launch * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(float2);
-    return align_up(f, 256) + align_up(p, 256) + canary_bytes;
+    return in_bytes(j) + align_up(f, 256) + align_up(p, 256) + canary_bytes;
   };
   size_t job_idx = 0;
   int rc;
@@ -463,6 +468,8 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     std::vector<ProjFieldF> fields;
     std::vector<std::vector<TcJob>> tjobs(sp.n_coef_sets, std::vector<TcJob>(nj));
     std::vector<uint32_t*> canaries;
+    std::vector<F32ConvSeg> segs;
+    long long max_seg = 0;
     char* ws = c->d_ws;
     long long unit = 0;
     for (int k = 0; k < nj; ++k) {
@@ -473,10 +480,25 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
         canaries.push_back(reinterpret_cast<uint32_t*>(at));
         at += kCanaryBytes;
       };
-      auto add_field = [&](const double2* phi, int nd, int n_terms, const int* offs,
+      // the job's inputs in FP32: V, then phi_1..3 packed
+      const float2* Vf = reinterpret_cast<const float2*>(base);
+      segs.push_back(F32ConvSeg{j.V, reinterpret_cast<float2*>(base), (long long)rows * n_ev});
+      max_seg = std::max(max_seg, (long long)rows * n_ev);
+      char* pb = base + align_up((size_t)rows * n_ev * sizeof(float2), 256);
+      const float2* phif[3];
+      for (int i = 0; i < 3; ++i) {
+        phif[i] = reinterpret_cast<const float2*>(pb);
+        const long long n = 4LL * n_ev * j.nd[i];
+        segs.push_back(F32ConvSeg{j.phi[i], reinterpret_cast<float2*>(pb), n});
+        max_seg = std::max(max_seg, n);
+        pb += (size_t)n * sizeof(float2);
+      }
+      base += in_bytes(j);
+      canary(base);
+      auto add_field = [&](const float2* phi, int nd, int n_terms, const int* offs,
                            const double2* w) -> float2* {
         ProjFieldF f{};
-        f.V = j.V;
+        f.V = Vf;
         f.phi = phi;
         f.q = reinterpret_cast<float2*>(base);
         f.nd = nd;
@@ -492,11 +514,11 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       const float2* q2[4] = {};
       for (int sl = 0; sl < sp.n1; ++sl) {
         int off = sp.alpha_of1[sl] * n_ev;
-        q1[sl] = add_field(j.phi[0], j.nd[0], 1, &off, &one);
+        q1[sl] = add_field(phif[0], j.nd[0], 1, &off, &one);
       }
       for (int sl = 0; sl < sp.n2; ++sl) {
         int off = sp.beta_of2[sl] * n_ev;
-        q2[sl] = add_field(j.phi[1], j.nd[1], 1, &off, &one);
+        q2[sl] = add_field(phif[1], j.nd[1], 1, &off, &one);
       }
       std::vector<std::vector<const float2*>> q3(sp.n_coef_sets, std::vector<const float2*>(sp.n_pairs));
       for (int set = 0; set < sp.n_coef_sets; ++set)
@@ -506,7 +528,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
           int offs[kMaxTerms];
           double2 w[kMaxTerms];
           for (size_t t = 0; t < tlist.size(); ++t) { offs[t] = tlist[t].first * n_ev; w[t] = tlist[t].second; }
-          q3[set][pr] = add_field(j.phi[2], j.nd[2], (int)tlist.size(), offs, w);
+          q3[set][pr] = add_field(phif[2], j.nd[2], (int)tlist.size(), offs, w);
         }
       base = c->d_ws + align_up((size_t)(base - c->d_ws), 256);
       float2* partial = reinterpret_cast<float2*>(base);
@@ -541,13 +563,18 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     for (uint32_t* cn : canaries)
       if (!within_workspace(c, cn, kCanaryBytes))
         return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: canary outside the workspace");
+    for (const F32ConvSeg& g : segs)
+      if (!within_workspace(c, g.dst, (size_t)g.n * sizeof(float2)))
+        return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: converted input outside the workspace");
     const size_t fbytes = align_up(fields.size() * sizeof(ProjFieldF), 256);
     const size_t jbytes = align_up((size_t)nj * sizeof(TcJob), 256);
-    const size_t cofs = fbytes + jbytes * sp.n_coef_sets;
+    const size_t sofs = fbytes + jbytes * sp.n_coef_sets;
+    const size_t cofs = sofs + align_up(segs.size() * sizeof(F32ConvSeg), 256);
     std::vector<char> tab(cofs + canaries.size() * sizeof(uint32_t*));
     memcpy(tab.data(), fields.data(), fields.size() * sizeof(ProjFieldF));
     for (int set = 0; set < sp.n_coef_sets; ++set)
       memcpy(tab.data() + fbytes + jbytes * set, tjobs[set].data(), (size_t)nj * sizeof(TcJob));
+    memcpy(tab.data() + sofs, segs.data(), segs.size() * sizeof(F32ConvSeg));
     if (!canaries.empty()) memcpy(tab.data() + cofs, canaries.data(), canaries.size() * sizeof(uint32_t*));
     rc = upload_tables(c, tab.data(), tab.size(), s);
     if (rc) return rc;
@@ -562,6 +589,10 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
         CK(c, cudaMemsetAsync(canaries[0], 0x5a, 4, s));
       }
     }
+    CK(c, timed_launch(c, K_CONVERT, s, [&] {
+      return launch_convert_f32(reinterpret_cast<const F32ConvSeg*>(c->d_tab + sofs),
+                                (int)segs.size(), max_seg, s);
+    }));
     CK(c, timed_launch(c, K_PROJECT, s, [&] {
       return launch_project_f32(d_fields, (int)fields.size(), rows, n_ev, max_ndf, c->opt_checks,
                                 c->d_dbg, c->d_status, s);

@@ -33,10 +33,11 @@ struct ProjField {
   double2 w[kMaxTerms];
 };
 
-// Same field, FP32 output for the tensor-core forms.
+// Same field for the tensor-core forms: V and phi are the FP32 copies made by
+// launch_convert_f32 (complex64), q is written in FP32.
 struct ProjFieldF {
-  const double2* V;
-  const double2* phi;
+  const float2* V;
+  const float2* phi;
   float2* q;
   int nd;
   int n_terms;
@@ -117,6 +118,14 @@ struct TcParams {
 
 enum TcForm { TC_BF16_3 = 0, TC_BF16_6 = 1, TC_BF16_9 = 2, TC_TF32_3 = 3 };
 
+// One input array of a call converted to FP32: n complex128 elements from src to dst.
+struct F32ConvSeg {
+  const double2* src;
+  float2* dst;
+  long long n;
+};
+cudaError_t launch_convert_f32(const F32ConvSeg* d_segs, int n_segs, long long max_n,
+                               cudaStream_t s);
 cudaError_t launch_project_f32(const ProjFieldF* d_fields, int n_fields, int rows, int n_ev,
                                int max_nd, int checks, unsigned long long* dbg, int* status,
                                cudaStream_t s);

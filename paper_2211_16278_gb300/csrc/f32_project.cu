@@ -1,10 +1,13 @@
 // Eq. (2) for the tensor-core forms: q = V^T Phi in FP32 with FP32 accumulation.
 //
-// The complex128 inputs are converted to FP32 while they are staged in shared memory (the
-// input-conversion step of the mixed forms); the spin coefficients of line 3 are folded
-// into the staged Phi tile as in the FP64 projection. One CTA computes a 128-row x 32-column
-// tile of one field; the grid runs the fields of a row tile back to back (blockIdx.x = field)
-// so that the V tile they share is served from L2.
+//   k_convert_f32   the input-conversion step of the mixed forms: every complex128 input
+//                   array of a call (each job's V and phi_i) to complex64, once per call,
+//                   in one launch over a segment table
+//   k_project_f32   q = V^T Phi from the FP32 copies; the spin coefficients of line 3 are
+//                   folded into the staged Phi tile as in the FP64 projection. One CTA
+//                   computes a 128-row x 32-column tile of one field; the grid runs the
+//                   fields of a row tile back to back (blockIdx.x = field) so that the V
+//                   tile they share is served from L2.
 #include "bblock_internal.h"
 
 namespace bb {
@@ -52,8 +55,7 @@ __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __re
       float2 v = make_float2(0.f, 0.f);
       if (l < n_ev && row < rows &&
           (!checks || f32_idx_ok((long long)l * rows + row, (long long)n_ev * rows, 11, blockIdx.x, dbg, status))) {
-        const double2 d = F.V[(size_t)l * rows + row];
-        v = make_float2((float)d.x, (float)d.y);
+        v = F.V[(size_t)l * rows + row];
       }
       As[kk][r] = v;
     }
@@ -66,8 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __re
           if (checks && !f32_idx_ok((long long)(F.row_off[t] + l) * nd + col, 4LL * n_ev * nd, 12,
                                     blockIdx.x, dbg, status))
             continue;
-          const double2 d = F.phi[(size_t)(F.row_off[t] + l) * nd + col];
-          const float2 f = make_float2((float)d.x, (float)d.y);
+          const float2 f = F.phi[(size_t)(F.row_off[t] + l) * nd + col];
           b.x = fmaf(wt[t].x, f.x, fmaf(-wt[t].y, f.y, b.x));
           b.y = fmaf(wt[t].x, f.y, fmaf(wt[t].y, f.x, b.y));
         }
@@ -104,6 +105,30 @@ __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __re
         F.q[(size_t)row * nd + col] = acc[i][j];
     }
   }
+}
+
+__global__ void k_convert_f32(const F32ConvSeg* __restrict__ segs) {
+  const F32ConvSeg sg = segs[blockIdx.y];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < sg.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 d = sg.src[i];
+    sg.dst[i] = make_float2((float)d.x, (float)d.y);
+  }
+}
+
+cudaError_t launch_convert_f32(const F32ConvSeg* d_segs, int n_segs, long long max_n,
+                               cudaStream_t s) {
+  if (n_segs == 0 || max_n == 0) return cudaSuccess;
+  for (int s0 = 0; s0 < n_segs; s0 += 65535) {  // grid.y limit
+    const int ns = n_segs - s0 < 65535 ? n_segs - s0 : 65535;
+    long long bx = (max_n + kThreads - 1) / kThreads;
+    if (bx > 1024) bx = 1024;
+    dim3 grid((unsigned)bx, ns);
+    k_convert_f32<<<grid, kThreads, 0, s>>>(d_segs + s0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_project_f32(const ProjFieldF* d_fields, int n_fields, int rows, int n_ev,
