@@ -74,6 +74,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU seconds of one oracle sample")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batched workload: skip the tile autotuner (heuristic tiles)")
     ap.add_argument("--no-triplet", action="store_true",
                     help="skip the mode-triplet ordering's measurement")
     ap.add_argument("--no-forms", action="store_true",
@@ -351,6 +353,8 @@ def run_ours(args):
     # useful complex GEMM work of the folded contraction: 8 M N K per job, K = 3 pairs X
     gemm_flops = sum(8.0 * nd[0] * nd[1] * (P * nd[2]) * (3 * pairs * w.X) for nd in job_nd)
 
+    tuned = {}
+
     def outputs():
         return [torch.empty((w.n_t, P, *inp.ndil[k]), dtype=torch.complex128, device=dev)
                 for k in range(w.n_noise)]
@@ -361,6 +365,19 @@ def run_ours(args):
         c = bb.bblock_create(w.L, w.n_ev, max_nd, precision, bf16_products=products,
                              device=local)
         outs = outputs()
+        if batched and not args.no_tune:
+            # tile shapes from the autotuner, timed on two time slices of the noise triple with
+            # the largest dilution; the slab count stays automatic for the whole batch
+            k = max(range(w.n_noise), key=lambda q: inp.ndil[q][0])
+            nt_s = min(2, w.n_t)
+            Bs = torch.empty((nt_s, P, *inp.ndil[k]), dtype=torch.complex128, device=dev)
+            rep = bb.bblock_autotune(c, V[:nt_s], *[p[:nt_s] for p in phis[k]], inp.momenta,
+                                     inp.spins, inp.coeffs, Bs, stream=stream, repeats=2)
+            bb.bblock_set_option(c, "slabs", 0)
+            tuned[form] = {"nc": bb.bblock_get_option(c, "tc_nc"),
+                           "chunk": bb.bblock_get_option(c, "tc_chunk"),
+                           "candidates_timed": sum(1 for r in rep if r["ms"] > 0)}
+            del Bs
         if batched:
             jobs = [(V[t], phis[k][0][t], phis[k][1][t], phis[k][2][t], outs[k][t])
                     for k in range(w.n_noise) for t in range(w.n_t)]
@@ -590,7 +607,8 @@ def run_ours(args):
                        "blocks_per_step_per_gpu": blocks_per_step,
                        "l2": "inputs larger than L2 (V %.0f MB, fields %.0f MB per step)" % (
                            inp.V.nbytes / 1e6, field_bytes / 1e6),
-                       "parallelism": f"{world} independent GPU(s), no collective"},
+                       "parallelism": f"{world} independent GPU(s), no collective",
+                       "tuned_tiles": tuned.get(head)},
             "algorithmic_tflops": (contract_alg + project_alg) * args.steps / (ms / 1e3) / 1e12,
             "gpu_launches": launches,
             "kernels": kernels,
