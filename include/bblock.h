@@ -190,6 +190,12 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 #define BBLOCK_OPT_FAIL_NEXT_ALLOC 8 /* test hook: 1 makes the next device allocation of the
                                        context fail as if the device were out of memory
                                        (BBLOCK_ERR_OOM), once */
+#define BBLOCK_OPT_TC_CLUSTER 10  /* BF16 tensor-core forms: CTAs of a thread-block cluster
+                                       sharing each 128-pair diquark tile, 2, 4 or 8 (each
+                                       builds 1/C of it and takes its own N tile; results are
+                                       bitwise those of the plain kernel with the same tiles);
+                                       0 (default) or 1: no clusters. Index checks and the
+                                       wait-limit test hook use no clusters */
 #define BBLOCK_OPT_CORRUPT_CANARY 9  /* test hook (with BBLOCK_OPT_CHECKS): 1 makes the next
                                        call overwrite its first canary from the host, in
                                        stream order between the fill and the check, once */

@@ -71,6 +71,7 @@ struct bblock_ctx {
   int opt_wait_us = 0;        // test hook: bounded-wait limit in microseconds (0: default)
   int opt_fail_alloc = 0;     // test hook: the next device allocation fails once
   int opt_corrupt_canary = 0; // test hook: the next call overwrites its first canary once
+  int opt_tc_cluster = 0;     // tensor-core cluster size: 0 automatic, 1 none, 2 / 4 / 8
   long long cycles_per_us = 2070;
 };
 
@@ -392,19 +393,41 @@ int tc_form_of(const bblock_config& cfg) {
 
 // Complex columns per tensor-core tile: the N tile that wastes the fewest padded columns,
 // counting a fixed per-tile cost of 16 columns for building the shared diquark tile.
-int choose_nc(const std::vector<JobIn>& jobs, size_t b, size_t e, int P) {
-  // tiles: 128 (d1, d2) pairs x nc (p, d3) columns
-  int best = 48;
-  long long best_cost = -1;
-  for (int nc = 48; nc >= 16; nc -= 16) {
-    long long cost = 0;
-    for (size_t k = b; k < e; ++k) {
-      const long long N = (long long)P * jobs[k].nd[2];
-      const long long mt = ((long long)jobs[k].nd[0] * jobs[k].nd[1] + 127) / 128;
-      cost += mt * ((N + nc - 1) / nc) * (nc + 16);
+struct TcTiling {
+  int cluster = 1;  // CTAs sharing one diquark tile (1: none)
+  int nc = 48;      // complex (p, d3) columns per CTA
+};
+
+// Cluster size and N tile for jobs [b, e).
+//
+// N tile: the widest that fits TMEM (48 complex columns) unless fewer, narrower tiles
+// cover the (p, d3) columns with less padding; every extra N tile rebuilds the 128-pair
+// diquark tile, the producers' dominant cost (a tile costs ~ 128 + nc row-units).
+// Cluster: no cluster unless the caller asks for one (BBLOCK_OPT_TC_CLUSTER). Measured on
+// GB300, clusters that share each diquark tile do not pay robustly: with 2 CTAs the whole
+// step is 2-4 % faster for the 3-piece BF16 forms at 448 columns (L = 48, 7 momenta,
+// N_dil = 64), 14 % slower for the 2-piece form, and unchanged at 96 or 320 columns;
+// clusters of 4 or 8 are slower, because the stage time barely falls with the diquark
+// work per CTA.
+TcTiling choose_tc_tiling(const bblock_ctx* c, const std::vector<JobIn>& jobs, size_t b,
+                          size_t e, int P, int form, int nc_fixed) {
+  const bool can_cluster = form != TC_TF32_3 && !c->opt_checks && c->opt_wait_us == 0 &&
+                           c->opt_tc_cluster != 1;
+  TcTiling best;
+  best.nc = nc_fixed > 0 ? nc_fixed : 48;
+  if (nc_fixed <= 0) {
+    long long best_cost = -1;
+    for (int nc = 48; nc >= 16; nc -= 16) {
+      long long cost = 0;
+      for (size_t k = b; k < e; ++k) {
+        const long long N = (long long)P * jobs[k].nd[2];
+        const long long mt = ((long long)jobs[k].nd[0] * jobs[k].nd[1] + 127) / 128;
+        cost += mt * ((N + nc - 1) / nc) * (nc + 128);
+      }
+      if (best_cost < 0 || cost < best_cost) { best_cost = cost; best.nc = nc; }
     }
-    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = nc; }
   }
+  if (can_cluster && c->opt_tc_cluster > 1) best.cluster = c->opt_tc_cluster;
   return best;
 }
 
@@ -447,17 +470,20 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       ++end;
     }
     const int nj = (int)(end - job_idx);
-    const int NC = c->opt_tc_nc > 0 ? c->opt_tc_nc : choose_nc(jobs, job_idx, end, P_launch);
+    const TcTiling tt = choose_tc_tiling(c, jobs, job_idx, end, P_launch, form, c->opt_tc_nc);
+    const int NC = tt.nc, CL = tt.cluster;
     long long tiles = 0, max_elems = 0;
     int max_ndf = 0;
     for (size_t k = job_idx; k < end; ++k) {
       const JobIn& j = jobs[k];
-      tiles += (long long)((j.nd[0] * j.nd[1] + 127) / 128) * ((P_launch * j.nd[2] + NC - 1) / NC);
+      // cluster units: one per (128-pair tile, group of CL N tiles)
+      tiles += (long long)((j.nd[0] * j.nd[1] + 127) / 128) *
+               ((P_launch * j.nd[2] + (long long)CL * NC - 1) / ((long long)CL * NC));
       for (int i = 0; i < 3; ++i) max_ndf = std::max(max_ndf, j.nd[i]);
       max_elems = std::max(max_elems, (long long)P_launch * j.nd[0] * j.nd[1] * j.nd[2]);
     }
     int n_slab = c->opt_slabs > 0 ? std::max(min_slabs, std::min(c->opt_slabs, X))
-                                   : std::max(min_slabs, choose_slabs(tiles, grid_cap, X, 1, max_slabs));
+                                   : std::max(min_slabs, choose_slabs(tiles, grid_cap / CL, X, 1, max_slabs));
     int sites_per_slab = (X + n_slab - 1) / n_slab;
     n_slab = (X + sites_per_slab - 1) / sites_per_slab;
     size_t ws_need = 0;
@@ -536,7 +562,8 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       canary(base);
       ws = base;
       const int m_tiles = (j.nd[0] * j.nd[1] + 127) / 128;           // (d1, d2) pairs
-      const int n_tiles = (P_launch * j.nd[2] + NC - 1) / NC;        // (p, d3) columns
+      // groups of CL N tiles of NC (p, d3) columns: a cluster unit covers one group
+      const int n_tiles = (P_launch * j.nd[2] + CL * NC - 1) / (CL * NC);
       for (int set = 0; set < sp.n_coef_sets; ++set) {
         TcJob& tj = tjobs[set][k];
         for (int i = 0; i < 4; ++i) { tj.q1[i] = q1[i]; tj.q2[i] = q2[i]; }
@@ -613,12 +640,14 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     prm.dbg = c->d_dbg;
     prm.wait_limit = c->opt_wait_us > 0 ? (long long)c->opt_wait_us * c->cycles_per_us
                                         : 4000000000LL;
-    const int grid = (int)std::min<long long>(unit, grid_cap);
+    // CTAs wanted: CL per cluster unit, at most one per SM (the launch caps it further at
+    // the clusters that can be resident at once)
+    const int grid = (int)std::min<long long>(unit * CL, grid_cap / CL * CL);
     for (int set = 0; set < sp.n_coef_sets; ++set) {
       const TcJob* d_jobs = reinterpret_cast<const TcJob*>(c->d_tab + fbytes + jbytes * set);
       prm.jobs = d_jobs;
       prm.phase = c->d_phase + (per_mom ? (size_t)set * X : 0);
-      CK(c, timed_launch(c, K_CONTRACT, s, [&] { return launch_contract_tc(prm, form, grid, s); }));
+      CK(c, timed_launch(c, K_CONTRACT, s, [&] { return launch_contract_tc(prm, form, CL, grid, s); }));
       CK(c, timed_launch(c, K_REDUCE, s, [&] {
         return launch_reduce_slabs_f32(d_jobs, nj, n_slab, P_launch, max_elems, c->opt_checks,
                                        c->d_dbg, c->d_status, s);
@@ -905,7 +934,7 @@ std::vector<uint64_t> call_signature(const bblock_ctx* c, const std::vector<JobI
               ((uint64_t)per_mom << 16) | ((uint64_t)c->opt_tc_nc << 24) |
               ((uint64_t)c->opt_tc_chunk << 32) | ((uint64_t)c->opt_slabs << 40));
   k.push_back((uint64_t)n_mom | ((uint64_t)n_spin << 32));
-  k.push_back((uint64_t)wave_budget(c));
+  k.push_back((uint64_t)wave_budget(c) ^ ((uint64_t)c->opt_tc_cluster << 60));
   for (int i = 0; i < 3 * n_mom; ++i) k.push_back((uint64_t)(uint32_t)momenta[i]);
   for (int i = 0; i < 3 * n_spin; ++i) k.push_back((uint64_t)(uint32_t)spin_idx[i]);
   const int n_coef = 2 * n_spin * (per_mom ? n_mom : 1);
@@ -1033,16 +1062,18 @@ CallPlan plan_call(const bblock_ctx* c, int n_t, const int nd[3], int n_mom, int
   const int max_slabs = std::max(64, min_slabs);
   std::vector<JobIn> one(1);
   one[0].nd[0] = nd[0]; one[0].nd[1] = nd[1]; one[0].nd[2] = nd[2];
-  pl.nc = nc_opt > 0 ? nc_opt : choose_nc(one, 0, 1, n_mom);
+  // the tiling run_jobs_tc would pick with this candidate's N tile
+  const TcTiling tt = choose_tc_tiling(c, one, 0, 1, n_mom, tc_form_of(c->cfg), nc_opt);
+  pl.nc = tt.nc;
   const long long N = (long long)n_mom * nd[2];                   // (p, d3) columns
-  const long long n_tiles = (N + pl.nc - 1) / pl.nc;
+  const long long n_tiles = (N + (long long)tt.cluster * pl.nc - 1) / ((long long)tt.cluster * pl.nc);
   const long long tiles = (long long)n_t * (((long long)nd[0] * nd[1] + 127) / 128) * n_tiles;
   int ns = slabs_opt > 0 ? std::max(min_slabs, std::min(slabs_opt, X))
-                         : std::max(min_slabs, choose_slabs(tiles, c->num_sms, X, 1, max_slabs));
+                         : std::max(min_slabs, choose_slabs(tiles, c->num_sms / tt.cluster, X, 1, max_slabs));
   const int sps = (X + ns - 1) / ns;
   pl.n_slab = (X + sps - 1) / sps;
   pl.units = tiles * pl.n_slab;
-  pl.pad = (double)(n_tiles * pl.nc) / N - 1.0;
+  pl.pad = (double)(n_tiles * tt.cluster * pl.nc) / N - 1.0;
   return pl;
 }
 
@@ -1567,6 +1598,10 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       if (value != 0 && value != 1) break;
       c->opt_fail_alloc = value;
       return BBLOCK_OK;
+    case BBLOCK_OPT_TC_CLUSTER:
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) break;
+      c->opt_tc_cluster = value;
+      return BBLOCK_OK;
     case BBLOCK_OPT_CORRUPT_CANARY:
       if (value != 0 && value != 1) break;
       c->opt_corrupt_canary = value;
@@ -1590,6 +1625,7 @@ int bblock_get_option(const bblock_ctx* c, int option) {
     case BBLOCK_OPT_WAIT_LIMIT_US: return c->opt_wait_us;
     case BBLOCK_OPT_FAIL_NEXT_ALLOC: return c->opt_fail_alloc;
     case BBLOCK_OPT_CORRUPT_CANARY: return c->opt_corrupt_canary;
+    case BBLOCK_OPT_TC_CLUSTER: return c->opt_tc_cluster;
     case BBLOCK_OPT_CHECKS: return c->opt_checks;
     default: return BBLOCK_ERR_INVALID_ARG;
   }

@@ -129,7 +129,9 @@ cudaError_t launch_convert_f32(const F32ConvSeg* d_segs, int n_segs, long long m
 cudaError_t launch_project_f32(const ProjFieldF* d_fields, int n_fields, int rows, int n_ev,
                                int max_nd, int checks, unsigned long long* dbg, int* status,
                                cudaStream_t s);
-cudaError_t launch_contract_tc(const TcParams& p, int form, int grid, cudaStream_t s);
+// cluster: 1 (plain kernel) or 2, 4, 8 CTAs sharing each diquark tile (BF16 forms, no
+// index checks); grid: CTAs wanted, capped at the clusters that fit at once
+cudaError_t launch_contract_tc(const TcParams& p, int form, int cluster, int grid, cudaStream_t s);
 int tc_groups_per_stage(int form);
 cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab, int P_total,
                                     long long max_elems, int checks, unsigned long long* dbg,

@@ -16,6 +16,15 @@
 // second accumulator. Each work unit (job, 128 pairs, NC columns, site slab) writes its
 // running sum as an FP32 partial block; the slab partials are summed in FP64 in index order.
 //
+// Clusters (BF16 forms): C CTAs of a thread-block cluster take the same (job, 128 pairs,
+// slab) and C neighbouring N tiles. Each builds only 128/C rows of the diquark tile and
+// pushes them into the other CTAs' stage buffers with bulk shared::cta -> shared::cluster
+// copies, counted as transaction bytes on the peers' stage barriers; each CTA's MMA
+// completion arrives on the stage-free barriers of all C CTAs (multicast commit). The
+// diquark is then built once per cluster instead of once per N tile. Measured, this pays
+// only for wide blocks (13 % at 448 columns with C = 2): the stage time barely falls with
+// the diquark work per CTA. C = 1 is the plain kernel.
+//
 // Warp roles: 0-3 epilogue (TMEM lanes 0-127: drains, partial write-out), 4 MMA issue and
 // TMEM allocation, 5.. operand producers (11 warps for BF16, 6 for TF32). Every wait is
 // bounded; on a timeout the CTA raises an abort flag and a status bit, the roles run out
@@ -37,14 +46,25 @@ constexpr int kTmemCols = 512;
 // Producer warps: one 8-group item per thread. BF16 stages hold 16 groups (two halves per
 // row): 8 warps build the 128-row diquark tile, 3 warps the <= 48-row third-quark tile.
 // TF32 stages hold 8 groups: 4 + 2 warps.
-template <bool TF32> struct Roles {
-  static constexpr int kAThreads = TF32 ? 128 : 256;
-  static constexpr int kBThreads = TF32 ? 64 : 96;
-  static constexpr int kProdThreads = kAThreads + kBThreads;
-  static constexpr int kThreads = kProdWarp0 * 32 + kProdThreads;
-};
 constexpr int kMaxNC = 48;
+// With a cluster of C CTAs each builds kARows = 128 / C diquark rows: one item per thread of
+// kAGroups groups (8 rows x 4 items per warp, one 8-row core-matrix group per warp, so that
+// a warp's rows are one contiguous 768-byte run per plane). Third-quark items hold
+// kBGroups groups. The producer warp count is fixed (11 BF16, 6 TF32); spare threads idle.
+template <bool TF32, int C> struct Roles {
+  static constexpr int G = TF32 ? 8 : 16;
+  static constexpr int kARows = kTcM / C;
+  static constexpr int kAGroups = C == 1 ? 8 : 4;
+  static constexpr int kBGroups = C <= 2 ? 8 : 4;
+  static constexpr int kAThreads = kARows * (G / kAGroups);
+  static constexpr int kBThreads = kMaxNC * (G / kBGroups);
+  static constexpr int kProdThreads = TF32 ? 192 : 352;
+  static constexpr int kThreads = kProdWarp0 * 32 + kProdThreads;
+  static_assert(kAThreads % 32 == 0 && kAThreads + kBThreads <= kProdThreads, "producer roles");
+  static_assert(!TF32 || C == 1, "clusters are built for the BF16 forms");
+};
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s: the default limit of every wait
+constexpr long long kDrainCycles = 20000000LL;   // about 10 ms: abort-path drain of peer copies
 constexpr int kBarProd = 1, kBarEpi = 2;
 constexpr int kAPlaneBytes = kTcM * 96;          // 128 rows x 96 bytes of K per stage
 constexpr int kBPlaneBytes = kMaxNC * 96;
@@ -139,6 +159,40 @@ __device__ __forceinline__ void tmem_wait_ld() {
 __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster (warp-aligned)
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// the shared::cluster address of this CTA's shared::cta address saddr in CTA `rank`
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+// bulk copy of `bytes` from this CTA's shared memory to a peer's; completion is counted as
+// transaction bytes on the peer's mbarrier
+__device__ __forceinline__ void copy_to_peer(uint32_t dst_cluster, uint32_t src, uint32_t bytes,
+                                             uint32_t mbar_cluster) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst_cluster), "r"(src), "r"(bytes), "r"(mbar_cluster) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t a, uint32_t tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(tx)
+               : "memory");
+}
+// MMA completion arriving on the same barrier of every CTA in `mask`
+__device__ __forceinline__ void tc_commit_multicast(uint32_t mbar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(mbar), "h"(mask) : "memory");
+}
 
 // ------------------------------------------------------------------ operand splitting
 
@@ -155,17 +209,18 @@ __device__ __forceinline__ float tf32_round(float v) {
 // every subtraction is exact and v2 has at most 8 significant bits, so v0 + v1 + v2 == v;
 // with two pieces the second is rounded to nearest (error <= 2^-17 |v|).
 // TF32: v0 = trunc11(v), v1 = rn_tf32(v - v0) (error <= 2^-21 |v|).
-template <bool TF32, int LEVELS>
+template <bool TF32, int LEVELS, int NG = 8>
 __device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const (&dst)[LEVELS]) {
+  static_assert(NG == 8 || (NG == 4 && !TF32), "K runs of 8 (BF16, TF32) or 4 (BF16) values");
   if (!TF32) {
     float r[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) r[i] = v[i];
+    for (int i = 0; i < NG; ++i) r[i] = v[i];
 #pragma unroll
     for (int l = 0; l < LEVELS; ++l) {
       uint32_t piece[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < NG; ++i) {
         if (l < LEVELS - 1) {
           piece[i] = __float_as_uint(r[i]) & 0xFFFF0000u;
           r[i] -= __uint_as_float(piece[i]);
@@ -176,12 +231,19 @@ __device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const
           piece[i] = (uint32_t)(*reinterpret_cast<const uint16_t*>(&h)) << 16;
         }
       }
-      uint4 w;
-      w.x = __byte_perm(piece[0], piece[1], 0x7632);
-      w.y = __byte_perm(piece[2], piece[3], 0x7632);
-      w.z = __byte_perm(piece[4], piece[5], 0x7632);
-      w.w = __byte_perm(piece[6], piece[7], 0x7632);
-      *reinterpret_cast<uint4*>(dst[l]) = w;
+      if (NG == 8) {
+        uint4 w;
+        w.x = __byte_perm(piece[0], piece[1], 0x7632);
+        w.y = __byte_perm(piece[2], piece[3], 0x7632);
+        w.z = __byte_perm(piece[4], piece[5], 0x7632);
+        w.w = __byte_perm(piece[6], piece[7], 0x7632);
+        *reinterpret_cast<uint4*>(dst[l]) = w;
+      } else {
+        uint2 w;
+        w.x = __byte_perm(piece[0], piece[1], 0x7632);
+        w.y = __byte_perm(piece[2], piece[3], 0x7632);
+        *reinterpret_cast<uint2*>(dst[l]) = w;
+      }
     }
   } else {
     float h[8], lo[8];
@@ -264,11 +326,13 @@ __device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t parity,
   }
 }
 
-template <bool TF32, int LEVELS, int NPROD, bool CHECKS>
-__global__ void __launch_bounds__(Roles<TF32>::kThreads, 1)
+template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C>
+__global__ void __launch_bounds__(Roles<TF32, C>::kThreads, 1)
 k_contract_tc(const __grid_constant__ TcParams prm) {
-  using R = Roles<TF32>;
+  using R = Roles<TF32, C>;
   constexpr int G = TF32 ? 8 : 16;                 // (site, pair) groups per stage
+  // transaction bytes a stage receives from the peers: their diquark rows, every plane
+  constexpr uint32_t kPeerTx = (uint32_t)((C - 1) * (R::kARows / 8) * 768 * LEVELS * 2);
   constexpr int STAGES = LEVELS == 3 ? 2 : 3;
   constexpr int STAGE_BYTES = LEVELS * 2 * (kAPlaneBytes + kBPlaneBytes);
   // piece products (i, j): leading (0, 0) first, then by increasing i + j
@@ -292,7 +356,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&bar_full[s]), R::kProdThreads / 32);   // one arrival per producer warp
-      mbar_init(smem_u32(&bar_empty[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), C);   // the MMA completion of every CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&bar_acc_full[b]), 1);
@@ -309,9 +373,13 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
   }
   tc_fence_before();
   __syncthreads();
+  if (C > 1) cluster_sync_all();   // peers signal this CTA's barriers only once they exist
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t smem_base = smem_u32(smem);
+  // work units are shared by the C CTAs of a cluster; rank r takes N tile (group * C + r)
+  const uint32_t rank = C > 1 ? cluster_rank() : 0u;
+  const long long u0 = blockIdx.x / C, du = gridDim.x / C;
 
   auto a_plane = [&](int stage, int level, int plane) -> uint32_t {
     return (uint32_t)(stage * STAGE_BYTES + (level * 2 + plane) * kAPlaneBytes);
@@ -326,16 +394,30 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
 
   if (warp >= kProdWarp0) {
     // ------------------------------------------------------------ producers
-    // Thread roles are fixed: pt < kAThreads builds diquark rows (M side), the rest build
-    // phase x third-quark rows (N side); each thread owns one row and 8 consecutive groups
-    // (half h) of every stage.
+    // Thread roles are fixed: pt < kAThreads builds diquark rows (M side), the next
+    // kBThreads build phase x third-quark rows (N side); each thread owns one row and NG
+    // consecutive groups (starting at g0) of every stage.
     const int pt = tid - kProdWarp0 * 32;
     const bool is_a = pt < R::kAThreads;
-    const int rr = is_a ? pt % kTcM : (pt - R::kAThreads) % kMaxNC;
-    const int h = is_a ? pt / kTcM : (pt - R::kAThreads) / kMaxNC;
-    const bool row_used = is_a || (rr < NC && h < G / 8);
+    const bool is_b = !is_a && pt < R::kAThreads + R::kBThreads;
+    int rr, g0;
+    if (is_a) {
+      if (C == 1) {
+        rr = pt % kTcM;
+        g0 = (pt / kTcM) * 8;
+      } else {   // 8 rows x 4 items per warp: the warp's rows are one core-matrix row group
+        rr = (int)rank * R::kARows + (pt / 32) * 8 + (lane >> 2);
+        g0 = (lane & 3) * 4;
+      }
+    } else {
+      const int b = is_b ? pt - R::kAThreads : 0;
+      rr = b % kMaxNC;
+      g0 = (b / kMaxNC) * R::kBGroups;
+    }
+    const int NG = is_a ? R::kAGroups : R::kBGroups;
+    const bool row_used = is_a || (is_b && rr < NC);
     long long s_g = 0;
-    for (long long u = blockIdx.x; u < prm.total_units; u += gridDim.x) {
+    for (long long u = u0; u < prm.total_units; u += du) {
       const Unit w = decode_unit(prm, u, G);
       const TcJob& J = prm.jobs[w.job];
       const int nd1 = J.nd1, nd2 = J.nd2, nd3 = J.nd3;
@@ -350,7 +432,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
         off1 = d1; off2 = d2; s1 = nd1; s2 = nd2;
       } else {
         // N side: phase x third quark of the column n = p * nd3 + d3
-        const int n = w.nt * NC + rr;
+        const int n = (w.nt * C + (int)rank) * NC + rr;
         row_ok = row_used && n < prm.P * nd3;
         const int p = row_ok ? n / nd3 : 0, d3 = row_ok ? n - p * nd3 : 0;
         off1 = d3; s1 = nd3; pidx = p;
@@ -375,13 +457,16 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
         if (ok && s_g >= STAGES)
           ok = wait_bounded(smem_u32(&bar_empty[slot]), (uint32_t)(((s_g / STAGES) + 1) & 1),
                             &abort_flag, prm.status, prm.wait_limit);
+        // a warp either fills its rows of this stage or (after an abort) none of them
+        ok = __all_sync(0xffffffffu, ok);
         if (ok && row_used) {
           float re[3][8], im[3][8];
-          // first group of this thread's run of 8
-          const int gi0 = st * G + h * 8;
+          // first group of this thread's run of NG
+          const int gi0 = st * G + g0;
           int xl = gi0 / np, pr = gi0 - xl * np;
 #pragma unroll
           for (int half = 0; half < 2; ++half) {
+            if (half * 4 >= NG) break;
             // 4 groups: issue every load first, then compute
             float2 ld[4][6];
             bool vld[4];
@@ -435,26 +520,59 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
               re[2][jj] = c2.x * z; im[2][jj] = c2.y * z;
             }
           }
-          // colour c occupies K bytes [32c, 32c + 32); this thread's 8 groups start at 16h
+          // colour c occupies K bytes [32c, 32c + 32) (BF16; TF32: [32c, 32c + 32) of each
+          // 8-group stage as well); group g sits in 16-byte column 2c + g / 8 at 2 (g % 8)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const int seg = 2 * c + h;
+            const int seg = 2 * c + g0 / 8;
+            const uint32_t in_row = TF32 ? 0u : (uint32_t)((g0 % 8) * 2);
             uint8_t* dr[LEVELS];
             uint8_t* di[LEVELS];
 #pragma unroll
             for (int l = 0; l < LEVELS; ++l) {
-              dr[l] = smem + (is_a ? a_plane(slot, l, 0) : b_plane(slot, l, 0)) + row_seg(rr, seg);
-              di[l] = smem + (is_a ? a_plane(slot, l, 1) : b_plane(slot, l, 1)) + row_seg(rr, seg);
+              dr[l] = smem + (is_a ? a_plane(slot, l, 0) : b_plane(slot, l, 0)) + row_seg(rr, seg) + in_row;
+              di[l] = smem + (is_a ? a_plane(slot, l, 1) : b_plane(slot, l, 1)) + row_seg(rr, seg) + in_row;
             }
-            split_store8<TF32, LEVELS>(re[c], dr);
-            split_store8<TF32, LEVELS>(im[c], di);
+            if constexpr (TF32) {
+              split_store8<TF32, LEVELS>(re[c], dr);
+              split_store8<TF32, LEVELS>(im[c], di);
+            } else {
+              if (NG == 8) {
+                split_store8<TF32, LEVELS>(re[c], dr);
+                split_store8<TF32, LEVELS>(im[c], di);
+              } else {
+                split_store8<TF32, LEVELS, 4>(re[c], dr);
+                split_store8<TF32, LEVELS, 4>(im[c], di);
+              }
+            }
           }
         }
         // every lane's core-matrix stores are made visible to the tensor core's (async)
-        // proxy; once the whole warp has fenced, one lane arrives for the warp
+        // proxy; once the whole warp has fenced, one lane acts for the warp
         fence_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bar_full[slot]));
+        if (lane == 0) {
+          if (C > 1 && is_a && ok) {
+            // this warp's 8 diquark rows (one row group) of every plane go to every peer
+            const uint32_t rg = (uint32_t)(rr >> 3);
+            const uint32_t full_local = smem_u32(&bar_full[slot]);
+            for (uint32_t q = 0; q < (uint32_t)C; ++q) {
+              if (q == rank) continue;
+              const uint32_t mbar = map_to_rank(full_local, q);
+#pragma unroll
+              for (int l = 0; l < LEVELS; ++l)
+#pragma unroll
+                for (int pl = 0; pl < 2; ++pl) {
+                  const uint32_t src = smem_base + a_plane(slot, l, pl) + rg * 768u;
+                  copy_to_peer(map_to_rank(src, q), src, 768u, mbar);
+                }
+            }
+          }
+          if (C > 1 && pt == 0)
+            mbar_arrive_expect_tx(smem_u32(&bar_full[slot]), kPeerTx);
+          else
+            mbar_arrive(smem_u32(&bar_full[slot]));
+        }
         __syncwarp();
       }
     }
@@ -467,7 +585,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
       const uint32_t idesc_neg = idesc | (1u << 14);
       long long s_g = 0, c_g = 0;
       bool stop = false;
-      for (long long u = blockIdx.x; u < prm.total_units && !stop; u += gridDim.x) {
+      for (long long u = u0; u < prm.total_units && !stop; u += du) {
         const Unit w = decode_unit(prm, u, G);
         for (int st = 0; st < w.n_stages; ++st, ++s_g) {
           const int slot = (int)(s_g % STAGES);
@@ -505,7 +623,10 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
               mma<TF32>(di, ai, br, idesc, 1u);
             }
           }
-          tc_commit(smem_u32(&bar_empty[slot]));
+          if (C > 1)
+            tc_commit_multicast(smem_u32(&bar_empty[slot]), (uint16_t)((1u << C) - 1u));
+          else
+            tc_commit(smem_u32(&bar_empty[slot]));
           if (chunk_last) {
             tc_commit(smem_u32(&bar_acc_full[buf]));
             ++c_g;
@@ -516,6 +637,15 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
       // abort: this wait ignores the abort flag and keeps the default limit
       tc_commit(smem_u32(&bar_final));
       wait_bounded(smem_u32(&bar_final), 0u, nullptr, prm.status, kWaitCycles);
+      if (C > 1 && stop) {
+        // after an abort, peers may still be copying into the stages this CTA no longer
+        // consumes: let those copies land (bounded) before the cluster leaves
+        for (int i = 0; i < STAGES; ++i) {
+          const long long k = s_g + i;
+          wait_bounded(smem_u32(&bar_full[k % STAGES]), (uint32_t)((k / STAGES) & 1), nullptr,
+                       prm.status, kDrainCycles);
+        }
+      }
     }
     __syncwarp();
   } else {
@@ -524,7 +654,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const uint32_t run_r = tmem + lane_base + (uint32_t)(8 * NC);
     long long c_g = 0;
-    for (long long u = blockIdx.x; u < prm.total_units; u += gridDim.x) {
+    for (long long u = u0; u < prm.total_units; u += du) {
       const Unit w = decode_unit(prm, u, G);
       const TcJob& J = prm.jobs[w.job];
       const int n_chunks = (w.n_stages + prm.chunk_stages - 1) / prm.chunk_stages;
@@ -569,7 +699,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
             if (m < M) {
 #pragma unroll
               for (int i = 0; i < 16; ++i) {
-                const int n = w.nt * NC + col + i;
+                const int n = (w.nt * C + (int)rank) * NC + col + i;
                 if (n < Ntot) {
                   const int p = n / nd3, d3 = n - p * nd3;
                   const size_t pi = (((size_t)w.slab * prm.P + p) * M + m) * nd3 + d3;
@@ -588,6 +718,8 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
   tc_fence_before();
   __syncwarp();
   __syncthreads();
+  // no CTA leaves while a peer may still address its shared memory
+  if (C > 1) cluster_sync_all();
   if (warp == kMmaWarp) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
@@ -595,21 +727,55 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
   }
 }
 
-template <bool TF32, int LEVELS, int NPROD, bool CHECKS>
+template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C>
 cudaError_t launch_variant(const TcParams& prm, int grid, cudaStream_t s) {
   constexpr int STAGES = LEVELS == 3 ? 2 : 3;
   const size_t smem = (size_t)STAGES * LEVELS * 2 * (kAPlaneBytes + kBPlaneBytes);
-  cudaError_t e = cudaFuncSetAttribute(k_contract_tc<TF32, LEVELS, NPROD, CHECKS>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = k_contract_tc<TF32, LEVELS, NPROD, CHECKS, C>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_contract_tc<TF32, LEVELS, NPROD, CHECKS><<<grid, Roles<TF32>::kThreads, smem, s>>>(prm);
+  if (C == 1) {
+    kern<<<grid, Roles<TF32, C>::kThreads, smem, s>>>(prm);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(Roles<TF32, C>::kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // as many clusters as can be resident at once (a cluster needs C SMs of one GPC)
+  cfg.gridDim = dim3((unsigned)grid);
+  int max_clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
+  if (e != cudaSuccess) return e;
+  if (max_clusters < 1) return cudaErrorInvalidConfiguration;
+  const long long want = (grid + C - 1) / C;
+  cfg.gridDim = dim3((unsigned)(C * (want < max_clusters ? want : max_clusters)));
+  e = cudaLaunchKernelEx(&cfg, kern, prm);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 template <bool TF32, int LEVELS, int NPROD>
-cudaError_t launch_form(const TcParams& prm, int grid, cudaStream_t s) {
-  return prm.checks ? launch_variant<TF32, LEVELS, NPROD, true>(prm, grid, s)
-                    : launch_variant<TF32, LEVELS, NPROD, false>(prm, grid, s);
+cudaError_t launch_form(const TcParams& prm, int cluster, int grid, cudaStream_t s) {
+  if (prm.checks) {
+    if (cluster != 1) return cudaErrorInvalidValue;
+    return launch_variant<TF32, LEVELS, NPROD, true, 1>(prm, grid, s);
+  }
+  if (TF32 && cluster != 1) return cudaErrorInvalidValue;
+  switch (cluster) {
+    case 1: return launch_variant<TF32, LEVELS, NPROD, false, 1>(prm, grid, s);
+    case 2: return launch_variant<TF32, LEVELS, NPROD, false, TF32 ? 1 : 2>(prm, grid, s);
+    case 4: return launch_variant<TF32, LEVELS, NPROD, false, TF32 ? 1 : 4>(prm, grid, s);
+    case 8: return launch_variant<TF32, LEVELS, NPROD, false, TF32 ? 1 : 8>(prm, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 __global__ void k_reduce_slabs_f32(const TcJob* __restrict__ jobs, int n_slab, int P_total,
@@ -633,15 +799,16 @@ __global__ void k_reduce_slabs_f32(const TcJob* __restrict__ jobs, int n_slab, i
 
 int tc_groups_per_stage(int form) { return form == TC_TF32_3 ? 8 : 16; }
 
-cudaError_t launch_contract_tc(const TcParams& prm, int form, int grid, cudaStream_t s) {
+cudaError_t launch_contract_tc(const TcParams& prm, int form, int cluster, int grid,
+                               cudaStream_t s) {
   if (prm.total_units == 0) return cudaSuccess;
   if (prm.NC < 16 || prm.NC > kMaxNC || prm.NC % 16 != 0 || prm.chunk_stages < 1)
     return cudaErrorInvalidValue;
   switch (form) {
-    case TC_BF16_3: return launch_form<false, 2, 3>(prm, grid, s);
-    case TC_BF16_6: return launch_form<false, 3, 6>(prm, grid, s);
-    case TC_BF16_9: return launch_form<false, 3, 9>(prm, grid, s);
-    case TC_TF32_3: return launch_form<true, 2, 3>(prm, grid, s);
+    case TC_BF16_3: return launch_form<false, 2, 3>(prm, cluster, grid, s);
+    case TC_BF16_6: return launch_form<false, 3, 6>(prm, cluster, grid, s);
+    case TC_BF16_9: return launch_form<false, 3, 9>(prm, cluster, grid, s);
+    case TC_TF32_3: return launch_form<true, 2, 3>(prm, cluster, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
