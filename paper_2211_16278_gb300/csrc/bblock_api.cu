@@ -24,7 +24,8 @@ struct bblock_ctx {
   int* d_status = nullptr;
   // phase cache
   std::vector<int32_t> phase_mom;
-  double2* d_phase = nullptr;
+  double2* d_phase = nullptr;     // FP64 phases [n_mom][X], then their FP32 copy
+  float2* d_phase_f = nullptr;
   size_t phase_cap = 0;
   int* d_mom = nullptr;
   size_t mom_cap = 0;
@@ -277,13 +278,15 @@ int plan_spins(bblock_ctx* c, const int32_t* spin_idx, const double* coeffs, int
 int ensure_phase(bblock_ctx* c, const int32_t* momenta, int n_mom, cudaStream_t s) {
   std::vector<int32_t> key(momenta, momenta + 3 * n_mom);
   if (c->d_phase && key == c->phase_mom) return BBLOCK_OK;
+  const size_t n_ph = (size_t)c->X * n_mom;
   int rc = grow_device(c, reinterpret_cast<char**>(&c->d_phase), &c->phase_cap,
-                       sizeof(double2) * (size_t)c->X * n_mom);
+                       (sizeof(double2) + sizeof(float2)) * n_ph);
   if (rc) return rc;
+  c->d_phase_f = reinterpret_cast<float2*>(c->d_phase + n_ph);
   rc = grow_device(c, reinterpret_cast<char**>(&c->d_mom), &c->mom_cap, sizeof(int) * 3 * n_mom);
   if (rc) return rc;
   CK(c, cudaMemcpyAsync(c->d_mom, momenta, sizeof(int) * 3 * n_mom, cudaMemcpyHostToDevice, s));
-  CK(c, timed_launch(c, K_PHASE, s, [&] { return launch_phase_table(c->cfg.L, n_mom, c->d_mom, c->d_phase, s); }));
+  CK(c, timed_launch(c, K_PHASE, s, [&] { return launch_phase_table(c->cfg.L, n_mom, c->d_mom, c->d_phase, c->d_phase_f, s); }));
   // the host momentum array may be reused by the caller right after return
   CK(c, cudaStreamSynchronize(s));
   c->phase_mom = key;
@@ -646,7 +649,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     for (int set = 0; set < sp.n_coef_sets; ++set) {
       const TcJob* d_jobs = reinterpret_cast<const TcJob*>(c->d_tab + fbytes + jbytes * set);
       prm.jobs = d_jobs;
-      prm.phase = c->d_phase + (per_mom ? (size_t)set * X : 0);
+      prm.phase = c->d_phase_f + (per_mom ? (size_t)set * X : 0);
       CK(c, timed_launch(c, K_CONTRACT, s, [&] { return launch_contract_tc(prm, form, CL, grid, s); }));
       CK(c, timed_launch(c, K_REDUCE, s, [&] {
         return launch_reduce_slabs_f32(d_jobs, nj, n_slab, P_launch, max_elems, c->opt_checks,

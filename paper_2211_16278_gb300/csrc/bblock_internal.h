@@ -103,7 +103,7 @@ struct TcParams {
   int n_pairs;
   int a_slot[kMaxPairs];
   int b_slot[kMaxPairs];
-  const double2* phase;          // [P][X]
+  const float2* phase;           // [P][X], the FP64 phases rounded to FP32
   int P;                         // momenta (columns n = p*nd3 + d3)
   int NC;                        // complex columns per tile: 16, 32 or 48
   int chunk_stages;              // stages accumulated in TMEM between drains
@@ -171,7 +171,9 @@ cudaError_t launch_zgemm(const ZgemmParams& p, cudaStream_t s);
 cudaError_t launch_canaries(uint32_t* const* d_list, int n, bool check, int* status,
                             cudaStream_t s);
 
-cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, cudaStream_t s);
+// ph: FP64 phases [n_mom][X]; ph_f (optional): the same rounded to FP32
+cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, float2* ph_f,
+                               cudaStream_t s);
 cudaError_t launch_project_fp64(const ProjField* d_fields, int n_fields, int rows, int n_ev,
                                 int max_nd, cudaStream_t s);
 cudaError_t launch_contract_fp64(const ContractParams& p, int P, int rn, int grid, cudaStream_t s);

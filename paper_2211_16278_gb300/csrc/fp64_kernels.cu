@@ -31,7 +31,7 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) {
 // ------------------------------------------------------------------ phases
 
 __global__ void k_phase_table(int L, int n_mom, const int* __restrict__ mom,
-                              double2* __restrict__ ph) {
+                              double2* __restrict__ ph, float2* __restrict__ ph_f) {
   const long long X = (long long)L * L * L;
   const long long total = X * n_mom;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -45,14 +45,16 @@ __global__ void k_phase_table(int L, int n_mom, const int* __restrict__ mom,
     double s, c;
     sincospi(2.0 * (double)k / (double)L, &s, &c);
     ph[i] = make_double2(c, -s);
+    if (ph_f) ph_f[i] = make_float2((float)c, (float)-s);
   }
 }
 
-cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, cudaStream_t s) {
+cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, float2* ph_f,
+                               cudaStream_t s) {
   const long long total = (long long)L * L * L * n_mom;
   if (total == 0) return cudaSuccess;
   const int grid = (int)((total + kThreads - 1) / kThreads < 65536 ? (total + kThreads - 1) / kThreads : 65536);
-  k_phase_table<<<grid, kThreads, 0, s>>>(L, n_mom, d_mom, ph);
+  k_phase_table<<<grid, kThreads, 0, s>>>(L, n_mom, d_mom, ph, ph_f);
   return cudaGetLastError();
 }
 

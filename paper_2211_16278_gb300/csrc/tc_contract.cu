@@ -8,8 +8,12 @@
 // Neither operand exists in HBM: producer warps build both in shared memory for every stage
 // of 16 (BF16) or 8 (TF32) (site, pair) groups, split each FP32 value into pieces
 // v = v0 + v1 (+ v2) and store them as K-major 8x16-byte core matrices; one thread issues
-// the MMAs. Complex products use separate real and imaginary planes:
-//   Cr += Ar Br - Ai Bi  (the second product with the B-negate bit),  Ci += Ar Bi + Ai Br.
+// the MMAs. Complex products use separate real and imaginary planes. In the three-piece
+// BF16 forms the third-quark operand is stored as -Bi | Br | Bi, and one complex product is
+// two MMAs of N = 2 NC:
+//   [Cr | Ci] += Ar [Br | Bi],   [Cr | Ci] += Ai [-Bi | Br];
+// the other forms, bound by their producers rather than by the MMAs, skip the -Bi plane and
+// take four MMAs of N = NC (the -Ai Bi product with the B-negate bit).
 // Accuracy: the TMEM accumulator rounds towards zero, so the leading piece product (v0 w0)
 // goes to its own accumulator and is drained every `chunk_stages` stages into an FP32
 // running sum (round to nearest) kept in TMEM; the smaller correction products share a
@@ -67,7 +71,24 @@ constexpr long long kWaitCycles = 4000000000LL;  // about 2 s: the default limit
 constexpr long long kDrainCycles = 20000000LL;   // about 10 ms: abort-path drain of peer copies
 constexpr int kBarProd = 1, kBarEpi = 2;
 constexpr int kAPlaneBytes = kTcM * 96;          // 128 rows x 96 bytes of K per stage
-constexpr int kBPlaneBytes = kMaxNC * 96;
+constexpr int kBPlaneBytes = kMaxNC * 96;        // room for one plane of up to 48 rows
+// The third-quark operand of each piece level holds three planes, -Bi | Br | Bi, each of NC
+// rows (NC * 96 bytes, so that consecutive planes continue one another's 8-row groups).
+// Then [Br | Bi] and [-Bi | Br] are both contiguous operands of 2 NC rows, and a complex
+// product takes two MMAs of N = 2 NC into the adjacent [Cr | Ci] accumulator columns:
+//   [Cr | Ci] += Ar [Br | Bi],   [Cr | Ci] += Ai [-Bi | Br].
+// Each reads the 128-row A tile once, half as often as four N = NC real products would.
+// Measured, this pays where the MMAs bound the stage (three BF16 pieces: 14 % at L = 48).
+// Where the producers bound it (two pieces, TF32) the extra -Bi stores and the larger
+// stages (less L1 for the producers' loads) cost 2-10 %: those forms keep two planes,
+// Br | Bi, and four MMAs of N = NC.
+template <bool TF32, int LEVELS> struct TcLayout {
+  static constexpr bool kTwoMma = !TF32 && LEVELS == 3;
+  static constexpr int kBPlanes = kTwoMma ? 3 : 2;
+  static constexpr int kBr = kTwoMma ? 1 : 0, kBi = kBr + 1;   // plane slots; -Bi is slot 0
+  static constexpr int kStages = LEVELS == 3 ? 2 : 3;
+  static constexpr int kStageBytes = LEVELS * (2 * kAPlaneBytes + kBPlanes * kBPlaneBytes);
+};
 constexpr int kSegsPerRow = 6;                   // 16-byte core-matrix columns per row
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -209,8 +230,12 @@ __device__ __forceinline__ float tf32_round(float v) {
 // every subtraction is exact and v2 has at most 8 significant bits, so v0 + v1 + v2 == v;
 // with two pieces the second is rounded to nearest (error <= 2^-17 |v|).
 // TF32: v0 = trunc11(v), v1 = rn_tf32(v - v0) (error <= 2^-21 |v|).
+// With `neg` set, the pieces of -v go to neg[l] as well: both splits are symmetric under
+// negation (truncation, round-to-nearest-even, TF32 round-half-away), so they are the
+// stored pieces with their sign bits flipped.
 template <bool TF32, int LEVELS, int NG = 8>
-__device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const (&dst)[LEVELS]) {
+__device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const (&dst)[LEVELS],
+                                             uint8_t* const* neg) {
   static_assert(NG == 8 || (NG == 4 && !TF32), "K runs of 8 (BF16, TF32) or 4 (BF16) values");
   if (!TF32) {
     float r[8];
@@ -238,11 +263,19 @@ __device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const
         w.z = __byte_perm(piece[4], piece[5], 0x7632);
         w.w = __byte_perm(piece[6], piece[7], 0x7632);
         *reinterpret_cast<uint4*>(dst[l]) = w;
+        if (neg) {
+          constexpr uint32_t m = 0x80008000u;
+          *reinterpret_cast<uint4*>(neg[l]) = make_uint4(w.x ^ m, w.y ^ m, w.z ^ m, w.w ^ m);
+        }
       } else {
         uint2 w;
         w.x = __byte_perm(piece[0], piece[1], 0x7632);
         w.y = __byte_perm(piece[2], piece[3], 0x7632);
         *reinterpret_cast<uint2*>(dst[l]) = w;
+        if (neg) {
+          constexpr uint32_t m = 0x80008000u;
+          *reinterpret_cast<uint2*>(neg[l]) = make_uint2(w.x ^ m, w.y ^ m);
+        }
       }
     }
   } else {
@@ -257,6 +290,12 @@ __device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const
     *reinterpret_cast<float4*>(dst[0] + 128) = make_float4(h[4], h[5], h[6], h[7]);
     *reinterpret_cast<float4*>(dst[1]) = make_float4(lo[0], lo[1], lo[2], lo[3]);
     *reinterpret_cast<float4*>(dst[1] + 128) = make_float4(lo[4], lo[5], lo[6], lo[7]);
+    if (neg) {
+      *reinterpret_cast<float4*>(neg[0]) = make_float4(-h[0], -h[1], -h[2], -h[3]);
+      *reinterpret_cast<float4*>(neg[0] + 128) = make_float4(-h[4], -h[5], -h[6], -h[7]);
+      *reinterpret_cast<float4*>(neg[1]) = make_float4(-lo[0], -lo[1], -lo[2], -lo[3]);
+      *reinterpret_cast<float4*>(neg[1] + 128) = make_float4(-lo[4], -lo[5], -lo[6], -lo[7]);
+    }
   }
 }
 
@@ -333,8 +372,14 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
   constexpr int G = TF32 ? 8 : 16;                 // (site, pair) groups per stage
   // transaction bytes a stage receives from the peers: their diquark rows, every plane
   constexpr uint32_t kPeerTx = (uint32_t)((C - 1) * (R::kARows / 8) * 768 * LEVELS * 2);
-  constexpr int STAGES = LEVELS == 3 ? 2 : 3;
-  constexpr int STAGE_BYTES = LEVELS * 2 * (kAPlaneBytes + kBPlaneBytes);
+  using Lay = TcLayout<TF32, LEVELS>;
+  constexpr int STAGES = Lay::kStages;
+  constexpr int STAGE_BYTES = Lay::kStageBytes;
+  constexpr bool kTwoMma = Lay::kTwoMma;   // complex product as two N = 2 NC MMAs
+  constexpr int kBPlanes = Lay::kBPlanes;
+  // groups whose loads a producer thread issues together before computing: all 8 in one
+  // round where the registers allow it; the cluster and checked variants would spill
+  constexpr int kLoadRun = (C == 1 && !CHECKS) ? 8 : 4;
   // piece products (i, j): leading (0, 0) first, then by increasing i + j
   constexpr int PI[9] = {0, 0, 1, 1, 0, 2, 1, 2, 2};
   constexpr int PJ[9] = {0, 1, 0, 1, 2, 0, 2, 1, 2};
@@ -384,9 +429,10 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
   auto a_plane = [&](int stage, int level, int plane) -> uint32_t {
     return (uint32_t)(stage * STAGE_BYTES + (level * 2 + plane) * kAPlaneBytes);
   };
+  // plane slots: -Bi = 0, Br = 1, Bi = 2 (two-MMA forms); Br = 0, Bi = 1 (the others)
   auto b_plane = [&](int stage, int level, int plane) -> uint32_t {
     return (uint32_t)(stage * STAGE_BYTES + LEVELS * 2 * kAPlaneBytes +
-                      (level * 2 + plane) * kBPlaneBytes);
+                      level * kBPlanes * kBPlaneBytes + plane * NC * 96);
   };
   auto row_seg = [](int r, int seg) -> uint32_t {
     return (uint32_t)(((r >> 3) * kSegsPerRow + seg) * 128 + (r & 7) * 16);
@@ -450,7 +496,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
       }
       __syncwarp();
       named_bar(kBarProd, R::kProdThreads);
-      const double2* phase_p = prm.phase + (size_t)pidx * prm.X;
+      const float2* phase_p = prm.phase + (size_t)pidx * prm.X;
       for (int st = 0; st < w.n_stages; ++st, ++s_g) {
         const int slot = (int)(s_g % STAGES);
         bool ok = !abort_flag;
@@ -464,14 +510,16 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
           // first group of this thread's run of NG
           const int gi0 = st * G + g0;
           int xl = gi0 / np, pr = gi0 - xl * np;
+          uint32_t vmask = 0;   // groups of this run that lie inside the slab and a used row
 #pragma unroll
-          for (int half = 0; half < 2; ++half) {
-            if (half * 4 >= NG) break;
-            // 4 groups: issue every load first, then compute
-            float2 ld[4][6];
-            bool vld[4];
+          for (int half = 0; half < 8 / kLoadRun; ++half) {
+            if (half * kLoadRun >= NG) break;
+            // kLoadRun groups: issue every load first, then compute
+            float2 ld[kLoadRun][6];
+            bool vld[kLoadRun];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < kLoadRun; ++j) {
+              if (half * kLoadRun + j >= NG) break;
               const int x = w.x_begin + xl;
               vld[j] = row_ok && x < w.x_end;
               int xs = vld[j] ? x : w.x_begin;
@@ -490,14 +538,14 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
                 ld[j][3] = vq[0]; ld[j][4] = vq[s2]; ld[j][5] = vq[2 * s2];
               } else {
                 const float2* q = s_q3[pr] + (size_t)xs * 3 * s1 + off1;
-                const double2 e = phase_p[xs];
                 ld[j][0] = q[0]; ld[j][1] = q[s1]; ld[j][2] = q[2 * s1];
-                ld[j][3] = make_float2((float)e.x, (float)e.y);
+                ld[j][3] = phase_p[xs];
               }
               if (++pr == np) { pr = 0; ++xl; }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < kLoadRun; ++j) {
+              if (half * kLoadRun + j >= NG) break;
               float2 c0, c1, c2;
               if (is_a) {
                 const float2 u0 = ld[j][0], u1 = ld[j][1], u2 = ld[j][2];
@@ -513,12 +561,23 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
                 c1 = cmulf(ld[j][3], ld[j][1]);
                 c2 = cmulf(ld[j][3], ld[j][2]);
               }
-              const float z = vld[j] ? 1.f : 0.f;
-              const int jj = half * 4 + j;
-              re[0][jj] = c0.x * z; im[0][jj] = c0.y * z;
-              re[1][jj] = c1.x * z; im[1][jj] = c1.y * z;
-              re[2][jj] = c2.x * z; im[2][jj] = c2.y * z;
+              const int jj = half * kLoadRun + j;
+              vmask |= (uint32_t)vld[j] << jj;
+              re[0][jj] = c0.x; im[0][jj] = c0.y;
+              re[1][jj] = c1.x; im[1][jj] = c1.y;
+              re[2][jj] = c2.x; im[2][jj] = c2.y;
             }
+          }
+          // groups past the slab's end or of an unused row (their loads read a valid site)
+          // contribute zeros; this branch is taken only at ragged edges
+          if (vmask != (1u << NG) - 1u) {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+              if (!((vmask >> jj) & 1u)) {
+                re[0][jj] = 0.f; im[0][jj] = 0.f;
+                re[1][jj] = 0.f; im[1][jj] = 0.f;
+                re[2][jj] = 0.f; im[2][jj] = 0.f;
+              }
           }
           // colour c occupies K bytes [32c, 32c + 32) (BF16; TF32: [32c, 32c + 32) of each
           // 8-group stage as well); group g sits in 16-byte column 2c + g / 8 at 2 (g % 8)
@@ -526,23 +585,28 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
           for (int c = 0; c < 3; ++c) {
             const int seg = 2 * c + g0 / 8;
             const uint32_t in_row = TF32 ? 0u : (uint32_t)((g0 % 8) * 2);
+            // A side: planes Ar, Ai. B side: Br, Bi, and -Bi beside them (plane 0).
             uint8_t* dr[LEVELS];
             uint8_t* di[LEVELS];
+            uint8_t* dn[LEVELS];
 #pragma unroll
             for (int l = 0; l < LEVELS; ++l) {
-              dr[l] = smem + (is_a ? a_plane(slot, l, 0) : b_plane(slot, l, 0)) + row_seg(rr, seg) + in_row;
-              di[l] = smem + (is_a ? a_plane(slot, l, 1) : b_plane(slot, l, 1)) + row_seg(rr, seg) + in_row;
+              const uint32_t o = row_seg(rr, seg) + in_row;
+              dr[l] = smem + (is_a ? a_plane(slot, l, 0) : b_plane(slot, l, Lay::kBr)) + o;
+              di[l] = smem + (is_a ? a_plane(slot, l, 1) : b_plane(slot, l, Lay::kBi)) + o;
+              dn[l] = smem + b_plane(slot, l, 0) + o;
             }
+            uint8_t* const* neg = (is_a || !kTwoMma) ? nullptr : dn;
             if constexpr (TF32) {
-              split_store8<TF32, LEVELS>(re[c], dr);
-              split_store8<TF32, LEVELS>(im[c], di);
+              split_store8<TF32, LEVELS>(re[c], dr, nullptr);
+              split_store8<TF32, LEVELS>(im[c], di, neg);
             } else {
               if (NG == 8) {
-                split_store8<TF32, LEVELS>(re[c], dr);
-                split_store8<TF32, LEVELS>(im[c], di);
+                split_store8<TF32, LEVELS>(re[c], dr, nullptr);
+                split_store8<TF32, LEVELS>(im[c], di, neg);
               } else {
-                split_store8<TF32, LEVELS, 4>(re[c], dr);
-                split_store8<TF32, LEVELS, 4>(im[c], di);
+                split_store8<TF32, LEVELS, 4>(re[c], dr, nullptr);
+                split_store8<TF32, LEVELS, 4>(im[c], di, neg);
               }
             }
           }
@@ -580,8 +644,10 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
     // ------------------------------------------------------------ MMA issue (one thread)
     if (lane == 0) {
       const uint32_t fmt = TF32 ? 2u : 1u;
+      // FP32 accumulate, A and B of the same type, K-major, M = 128, N = 2 NC or NC
+      const uint32_t n_mma = kTwoMma ? 2 * NC : NC;
       const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) |
-                             ((uint32_t)(NC >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+                             ((n_mma >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
       const uint32_t idesc_neg = idesc | (1u << 14);
       long long s_g = 0, c_g = 0;
       bool stop = false;
@@ -600,8 +666,8 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
           if (!wait_bounded(smem_u32(&bar_full[slot]), (uint32_t)((s_g / STAGES) & 1),
                             &abort_flag, prm.status, prm.wait_limit)) { stop = true; break; }
           tc_fence_after();
-          const uint32_t lead_r = tmem + (uint32_t)(buf * 4 * NC);
-          const uint32_t lead_i = lead_r + NC, corr_r = lead_r + 2 * NC, corr_i = lead_r + 3 * NC;
+          // [Cr | Ci] of the leading product, then of the correction products
+          const uint32_t lead = tmem + (uint32_t)(buf * 4 * NC), corr = lead + 2 * NC;
           const uint32_t sa = smem_base + (uint32_t)(slot * STAGE_BYTES);
           const uint32_t sb = sa + LEVELS * 2 * kAPlaneBytes;
 #pragma unroll
@@ -612,15 +678,23 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
             for (int q = 0; q < NPROD; ++q) {
               const uint64_t ar = smem_desc(sa + (PI[q] * 2 + 0) * kAPlaneBytes + kofs);
               const uint64_t ai = smem_desc(sa + (PI[q] * 2 + 1) * kAPlaneBytes + kofs);
-              const uint64_t br = smem_desc(sb + (PJ[q] * 2 + 0) * kBPlaneBytes + kofs);
-              const uint64_t bi = smem_desc(sb + (PJ[q] * 2 + 1) * kBPlaneBytes + kofs);
-              const uint32_t dr = q == 0 ? lead_r : corr_r;
-              const uint32_t di = q == 0 ? lead_i : corr_i;
+              const uint32_t bl = sb + (uint32_t)(PJ[q] * kBPlanes * kBPlaneBytes);
+              const uint32_t d = q == 0 ? lead : corr;
               const uint32_t acc = (q <= 1) ? first : 1u;
-              mma<TF32>(dr, ar, br, idesc, acc);
-              mma<TF32>(dr, ai, bi, idesc_neg, 1u);
-              mma<TF32>(di, ar, bi, idesc, acc);
-              mma<TF32>(di, ai, br, idesc, 1u);
+              if constexpr (kTwoMma) {
+                const uint64_t b_ri = smem_desc(bl + (uint32_t)(NC * 96) + kofs);   // [Br | Bi]
+                const uint64_t b_nr = smem_desc(bl + kofs);                         // [-Bi | Br]
+                mma<TF32>(d, ar, b_ri, idesc, acc);
+                mma<TF32>(d, ai, b_nr, idesc, 1u);
+              } else {
+                const uint64_t br = smem_desc(bl + (uint32_t)(Lay::kBr * NC * 96) + kofs);
+                const uint64_t bi = smem_desc(bl + (uint32_t)(Lay::kBi * NC * 96) + kofs);
+                const uint32_t di = d + (uint32_t)NC;
+                mma<TF32>(d, ar, br, idesc, acc);
+                mma<TF32>(d, ai, bi, idesc_neg, 1u);
+                mma<TF32>(di, ar, bi, idesc, acc);
+                mma<TF32>(di, ai, br, idesc, 1u);
+              }
             }
           }
           if (C > 1)
@@ -729,8 +803,8 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
 
 template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C>
 cudaError_t launch_variant(const TcParams& prm, int grid, cudaStream_t s) {
-  constexpr int STAGES = LEVELS == 3 ? 2 : 3;
-  const size_t smem = (size_t)STAGES * LEVELS * 2 * (kAPlaneBytes + kBPlaneBytes);
+  using Lay = TcLayout<TF32, LEVELS>;
+  const size_t smem = (size_t)Lay::kStages * Lay::kStageBytes;
   auto kern = k_contract_tc<TF32, LEVELS, NPROD, CHECKS, C>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
