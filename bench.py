@@ -579,8 +579,13 @@ def run_ours(args):
         for _ in range(args.steps):
             e2e_step()
         dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        # the host path computes in chunks of time slices, whose site slabs may differ from
+        # the device call's: the two agree to the form's rounding, not bit for bit
+        tol = 1e-12 if head in ("fp64", "df64") else 1e-5
         for h, o in zip(hB, outs):
-            assert np.array_equal(h.numpy(), o.cpu().numpy()), "host and device paths differ"
+            ref = o.cpu().numpy()
+            err = np.linalg.norm(h.numpy() - ref) / max(np.linalg.norm(ref), 1e-300)
+            assert err <= tol, f"host and device paths differ by {err:.2e}"
         h2d = hV.numel() * 16 + sum(p.numel() * 16 for ph in hphi for p in ph)
         e2e = {"value": job_throughput(world, blocks_per_step, args.steps, dt), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": sum(h.numel() * 16 for h in hB)}

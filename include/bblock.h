@@ -107,9 +107,12 @@ int bblock_compute(bblock_ctx* ctx, int n_t, const void* V, const void* phi1, co
                    int coeff_per_mom, void* B_out, void* stream);
 
 /* Same computation from HOST buffers: copies V and phi_i to context-owned device
- * buffers on `stream`, computes, copies B back into the host buffer B_out and
- * synchronises the stream before returning. Page-locked host memory
- * (cudaHostAlloc / pin_memory) gives full copy bandwidth; pageable memory works. */
+ * buffers, computes on `stream`, copies B back into the host buffer B_out and
+ * synchronises before returning. The time slices move in up to 8 chunks on a
+ * context-owned copy stream, so that the copies of one chunk overlap the
+ * computation of another (the slices are independent). Page-locked host memory
+ * (cudaHostAlloc / pin_memory) gives full copy bandwidth and overlap; pageable
+ * memory works. */
 int bblock_compute_host(bblock_ctx* ctx, int n_t, const void* V, const void* phi1,
                         const void* phi2, const void* phi3, int nd1, int nd2, int nd3,
                         const int32_t* momenta, int n_mom, const int32_t* spin_idx,
@@ -199,6 +202,11 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 #define BBLOCK_OPT_CORRUPT_CANARY 9  /* test hook (with BBLOCK_OPT_CHECKS): 1 makes the next
                                        call overwrite its first canary from the host, in
                                        stream order between the fill and the check, once */
+#define BBLOCK_OPT_HOST_CHUNKS 11  /* bblock_compute_host: chunks of time slices whose copies
+                                       overlap the computation, 1..64 (0, the default: 8). With
+                                       1 the blocks equal those of bblock_compute bit for bit;
+                                       with more, a chunk may split its sites into other slabs,
+                                       which changes the rounding only */
 #define BBLOCK_OPT_WAVE_MB 6   /* workspace budget of one wave of jobs, MiB: a batch whose
                                   fields and partial blocks exceed it runs as several waves
                                   of launches; 0 (default): half the device memory free at

@@ -38,9 +38,10 @@ struct bblock_ctx {
   char* h_tab = nullptr;
   size_t h_tab_cap = 0;
   cudaEvent_t tab_free = nullptr;
-  // device staging for bblock_compute_host
+  // device staging for bblock_compute_host, and the stream its copies run on
   char* d_io = nullptr;
   size_t io_cap = 0;
+  cudaStream_t copy_stream = nullptr;
   // mode-triplet ordering: identity coefficients [4 n_ev][n_ev] and the mode-product
   // intermediates (folded phi3, T x3 phi3', then x2 phi2)
   double2* d_ident = nullptr;
@@ -73,10 +74,13 @@ struct bblock_ctx {
   int opt_fail_alloc = 0;     // test hook: the next device allocation fails once
   int opt_corrupt_canary = 0; // test hook: the next call overwrites its first canary once
   int opt_tc_cluster = 0;     // tensor-core cluster size: 0 automatic, 1 none, 2 / 4 / 8
+  int opt_host_chunks = 0;    // bblock_compute_host chunks of time slices (0: kHostChunks)
   long long cycles_per_us = 2070;
 };
 
 namespace {
+// bblock_compute_host moves its time slices in at most this many chunks
+constexpr int kHostChunks = 8;
 enum KernelKind { K_PHASE = 0, K_PROJECT, K_CONTRACT, K_REDUCE, K_CONVERT, K_CANARY, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"phase", "project", "contract", "reduce", "convert",
                                            "canary"};
@@ -1163,6 +1167,7 @@ void bblock_destroy(bblock_ctx* c) {
   cudaFree(c->d_ws);
   cudaFree(c->d_tab);
   cudaFree(c->d_io);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   cudaFree(c->d_ident);
   cudaFree(c->d_tri);
   if (c->h_tab) cudaFreeHost(c->h_tab);
@@ -1431,16 +1436,72 @@ int bblock_compute_host(bblock_ctx* c, int n_t, const void* V, const void* phi1,
   rc = grow_device(c, &c->d_io, &c->io_cap, off[4] + align_up(bb_, 256));
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  CK(c, cudaMemcpyAsync(c->d_io + off[0], V, vb, cudaMemcpyHostToDevice, s));
-  CK(c, cudaMemcpyAsync(c->d_io + off[1], phi1, pb[0], cudaMemcpyHostToDevice, s));
-  CK(c, cudaMemcpyAsync(c->d_io + off[2], phi2, pb[1], cudaMemcpyHostToDevice, s));
-  CK(c, cudaMemcpyAsync(c->d_io + off[3], phi3, pb[2], cudaMemcpyHostToDevice, s));
-  rc = bblock_compute(c, n_t, c->d_io + off[0], c->d_io + off[1], c->d_io + off[2], c->d_io + off[3],
-                      nd1, nd2, nd3, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom,
-                      c->d_io + off[4], stream);
+  if (!c->copy_stream) CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = c->copy_stream;
+  // Time slices are independent, so the call runs in chunks of them: every chunk's inputs
+  // are enqueued at once on the copy stream, each chunk is computed on `stream` as soon as
+  // its inputs have landed, and its blocks go back while later chunks compute. Only the
+  // first chunk's inputs and the last chunk's blocks are exposed.
+  const int n_chunks = std::min(n_t, c->opt_host_chunks > 0 ? c->opt_host_chunks : kHostChunks);
+  std::vector<cudaEvent_t> ev(2 * n_chunks + 2, nullptr);
+  for (auto& e : ev)
+    if (!(e = take_event(c))) {
+      for (auto x : ev) if (x) c->ev_pool.push_back(x);
+      return fail(c, BBLOCK_ERR_CUDA, "cudaEventCreate failed");
+    }
+  auto give_back = [&] { for (auto x : ev) c->ev_pool.push_back(x); };
+  auto t_of = [&](int k) { return (long long)n_t * k / n_chunks; };
+  const size_t v_t = vb / n_t, b_t = bb_ / n_t;
+  size_t p_t[3];
+  for (int i = 0; i < 3; ++i) p_t[i] = pb[i] / n_t;
+  const void* hp[3] = {phi1, phi2, phi3};
+  // the staging may still be read by work the caller enqueued earlier on `stream`
+  cudaError_t e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+  for (int k = 0; k < n_chunks && e == cudaSuccess; ++k) {
+    const long long t0 = t_of(k), nt = t_of(k + 1) - t0;
+    e = cudaMemcpyAsync(c->d_io + off[0] + t0 * v_t, static_cast<const char*>(V) + t0 * v_t,
+                        nt * v_t, cudaMemcpyHostToDevice, cs);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(c->d_io + off[1 + i] + t0 * p_t[i],
+                          static_cast<const char*>(hp[i]) + t0 * p_t[i], nt * p_t[i],
+                          cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + k], cs);
+  }
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(cs);
+    give_back();
+    return cuda_fail(c, e, "enqueueing the input copies");
+  }
+  int launches = 0;
+  for (int k = 0; k < n_chunks && rc == BBLOCK_OK && e == cudaSuccess; ++k) {
+    const long long t0 = t_of(k), nt = t_of(k + 1) - t0;
+    e = cudaStreamWaitEvent(s, ev[1 + k], 0);
+    if (e != cudaSuccess) break;
+    rc = bblock_compute(c, (int)nt, c->d_io + off[0] + t0 * v_t, c->d_io + off[1] + t0 * p_t[0],
+                        c->d_io + off[2] + t0 * p_t[1], c->d_io + off[3] + t0 * p_t[2], nd1, nd2,
+                        nd3, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom,
+                        c->d_io + off[4] + t0 * b_t, stream);
+    if (rc) break;
+    launches += c->last_launches;
+    e = cudaEventRecord(ev[1 + n_chunks + k], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[1 + n_chunks + k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(static_cast<char*>(B_out) + t0 * b_t, c->d_io + off[4] + t0 * b_t,
+                          nt * b_t, cudaMemcpyDeviceToHost, cs);
+  }
+  // both streams drain before the call returns, also after an error
+  cudaError_t e2 = cudaEventRecord(ev[2 * n_chunks + 1], cs);
+  if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, ev[2 * n_chunks + 1], 0);
+  cudaError_t e3 = cudaStreamSynchronize(cs);
+  cudaError_t e4 = cudaStreamSynchronize(s);
+  give_back();
   if (rc) return rc;
-  CK(c, cudaMemcpyAsync(B_out, c->d_io + off[4], bb_, cudaMemcpyDeviceToHost, s));
-  CK(c, cudaStreamSynchronize(s));
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = e3;
+  if (e == cudaSuccess) e = e4;
+  if (e != cudaSuccess) return cuda_fail(c, e, "pipelined host copies");
+  c->last_launches = launches;
   return BBLOCK_OK;
 }
 
@@ -1605,6 +1666,10 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) break;
       c->opt_tc_cluster = value;
       return BBLOCK_OK;
+    case BBLOCK_OPT_HOST_CHUNKS:
+      if (value < 0 || value > 64) break;
+      c->opt_host_chunks = value;
+      return BBLOCK_OK;
     case BBLOCK_OPT_CORRUPT_CANARY:
       if (value != 0 && value != 1) break;
       c->opt_corrupt_canary = value;
@@ -1629,6 +1694,7 @@ int bblock_get_option(const bblock_ctx* c, int option) {
     case BBLOCK_OPT_FAIL_NEXT_ALLOC: return c->opt_fail_alloc;
     case BBLOCK_OPT_CORRUPT_CANARY: return c->opt_corrupt_canary;
     case BBLOCK_OPT_TC_CLUSTER: return c->opt_tc_cluster;
+    case BBLOCK_OPT_HOST_CHUNKS: return c->opt_host_chunks;
     case BBLOCK_OPT_CHECKS: return c->opt_checks;
     default: return BBLOCK_ERR_INVALID_ARG;
   }

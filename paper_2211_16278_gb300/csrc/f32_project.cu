@@ -5,9 +5,11 @@
 //                   in one launch over a segment table
 //   k_project_f32   q = V^T Phi from the FP32 copies; the spin coefficients of line 3 are
 //                   folded into the staged Phi tile as in the FP64 projection. One CTA
-//                   computes a 128-row x 32-column tile of one field; the grid runs the
-//                   fields of a row tile back to back (blockIdx.x = field) so that the V
-//                   tile they share is served from L2.
+//                   computes a 128-row x 32-column tile of one field (4 x 4 adjacent
+//                   outputs per thread, the next K block's loads in flight while the
+//                   current one is multiplied); the grid runs the fields of a row tile back
+//                   to back (blockIdx.x = field) so that the V tile they share is served
+//                   from L2.
 #include "bblock_internal.h"
 
 namespace bb {
@@ -29,37 +31,38 @@ __device__ __forceinline__ bool f32_idx_ok(long long i, long long n, int code, i
 __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __restrict__ fields,
                                                           int rows, int n_ev, int checks,
                                                           unsigned long long* dbg, int* status) {
-  __shared__ float2 As[FBK][FBM];
-  __shared__ float2 Bs[FBK][FBN];
+  __shared__ __align__(16) float2 As[FBK][FBM];
+  __shared__ __align__(16) float2 Bs[FBK][FBN];
   const ProjFieldF& F = fields[blockIdx.x];
   const int nd = F.nd;
   const int n0 = blockIdx.z * FBN;
   if (n0 >= nd) return;
   const int m0 = blockIdx.y * FBM;
-  const int tid = threadIdx.x, tn = tid % 8, tm = tid / 8;   // 32 x 8 threads, 4 x 4 outputs each
+  // 32 x 8 threads; each owns 4 adjacent rows x 4 adjacent columns, read from shared memory
+  // as two 16-byte loads per operand and k
+  const int tid = threadIdx.x, tn = tid % 8, tm = tid / 8;
   const int n_terms = F.n_terms;
   float2 wt[kMaxTerms];
   for (int t = 0; t < kMaxTerms; ++t)
     wt[t] = make_float2((float)F.w[t].x, (float)F.w[t].y);
-
-  float2 acc[4][4];
+  // staging of one K block: 8 V elements and 2 folded Phi elements per thread
+  constexpr int kAPer = FBK * FBM / kThreads, kBPer = FBK * FBN / kThreads;
+  float2 va[kAPer], vb[kBPer];
+  auto load_block = [&](int kb) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-
-  for (int kb = 0; kb < n_ev; kb += FBK) {
-    for (int idx = tid; idx < FBK * FBM; idx += kThreads) {
+    for (int j = 0; j < kAPer; ++j) {
+      const int idx = tid + kThreads * j;
       const int r = idx % FBM, kk = idx / FBM;
       const int l = kb + kk, row = m0 + r;
       float2 v = make_float2(0.f, 0.f);
       if (l < n_ev && row < rows &&
-          (!checks || f32_idx_ok((long long)l * rows + row, (long long)n_ev * rows, 11, blockIdx.x, dbg, status))) {
+          (!checks || f32_idx_ok((long long)l * rows + row, (long long)n_ev * rows, 11, blockIdx.x, dbg, status)))
         v = F.V[(size_t)l * rows + row];
-      }
-      As[kk][r] = v;
+      va[j] = v;
     }
-    for (int idx = tid; idx < FBK * FBN; idx += kThreads) {
+#pragma unroll
+    for (int j = 0; j < kBPer; ++j) {
+      const int idx = tid + kThreads * j;
       const int c = idx % FBN, kk = idx / FBN;
       const int l = kb + kk, col = n0 + c;
       float2 b = make_float2(0.f, 0.f);
@@ -73,16 +76,41 @@ __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __re
           b.y = fmaf(wt[t].x, f.y, fmaf(wt[t].y, f.x, b.y));
         }
       }
-      Bs[kk][c] = b;
+      vb[j] = b;
     }
+  };
+  auto store_block = [&] {
+#pragma unroll
+    for (int j = 0; j < kAPer; ++j) {
+      const int idx = tid + kThreads * j;
+      As[idx / FBM][idx % FBM] = va[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kBPer; ++j) {
+      const int idx = tid + kThreads * j;
+      Bs[idx / FBN][idx % FBN] = vb[j];
+    }
+  };
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  load_block(0);
+  for (int kb = 0; kb < n_ev; kb += FBK) {
+    store_block();
     __syncthreads();
+    // the next block's global loads are in flight while this block is multiplied
+    if (kb + FBK < n_ev) load_block(kb + FBK);
 #pragma unroll 4
     for (int kk = 0; kk < FBK; ++kk) {
-      float2 a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][tm + 32 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tn + 8 * j];
+      const float4* ar = reinterpret_cast<const float4*>(&As[kk][4 * tm]);
+      const float4* br = reinterpret_cast<const float4*>(&Bs[kk][4 * tn]);
+      const float4 a01 = ar[0], a23 = ar[1], b01 = br[0], b23 = br[1];
+      const float2 a[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w),
+                           make_float2(a23.x, a23.y), make_float2(a23.z, a23.w)};
+      const float2 b[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w),
+                           make_float2(b23.x, b23.y), make_float2(b23.z, b23.w)};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -95,18 +123,17 @@ __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __re
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int row = m0 + tm + 32 * i;
+    const int row = m0 + 4 * tm + i;
     if (row >= rows) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int col = n0 + tn + 8 * j;
+      const int col = n0 + 4 * tn + j;
       if (col < nd && (!checks || f32_idx_ok((long long)row * nd + col, (long long)rows * nd, 13,
                                               blockIdx.x, dbg, status)))
         F.q[(size_t)row * nd + col] = acc[i][j];
     }
   }
 }
-
 __global__ void k_convert_f32(const F32ConvSeg* __restrict__ segs) {
   const F32ConvSeg sg = segs[blockIdx.y];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < sg.n;

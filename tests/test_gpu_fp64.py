@@ -166,6 +166,46 @@ def test_host_entry_point_matches_device_entry_point(bb, torch_cuda):
     bb.bblock_destroy(ctx)
 
 
+@pytest.mark.parametrize("n_t", [3, 11])
+@pytest.mark.parametrize("precision", ["fp64", "df64", "bf16"])
+def test_host_entry_point_in_uneven_chunks(bb, torch_cuda, n_t, precision):
+    """The host entry point moves the time slices in up to 8 chunks on its own copy stream:
+    11 slices make chunks of 1 and 2, 3 slices one chunk each. A chunk may split its sites
+    into other slabs than a call over all slices, so the blocks agree with the device entry
+    point and the oracle to the form's tolerance; repeated host calls agree bit for bit.
+    Per-momentum coefficients check that each chunk pairs its slices with the right set."""
+    mom = [(0, 0, 0), (1, 1, 0), (0, 0, 1)]
+    inp = workloads.custom(3, 7, (6, 5, 4), n_t, mom, [(0, 1, 0), (1, 0, 0)], [0.5, -0.5],
+                           seed=40 + n_t)
+    coeffs = np.array([[0.5, -0.5], [0.3 + 0.1j, 0.7], [-1.0j, 0.25]])
+    tol = 1e-6 if precision == "bf16" else 1e-12
+    dev_out = run_gpu(bb, torch_cuda, inp, precision=precision, coeffs=coeffs)
+    ref = oracle_blocks(inp, coeffs=coeffs)
+    ctx = bb.bblock_create(3, 7, 6, precision)
+    stream = torch_cuda.cuda.Stream()
+    first = None
+    for _ in range(3):
+        B = np.full((n_t, 3, 6, 5, 4), np.nan, np.complex128)
+        bb.bblock_compute_host(ctx, inp.V, *[inp.phi[0][i] for i in range(3)], inp.momenta,
+                               inp.spins, coeffs, B, stream)
+        for t in range(n_t):
+            assert np.linalg.norm(B[t] - ref[t]) <= tol * np.linalg.norm(ref[t])
+        assert np.linalg.norm(B - dev_out) <= tol * np.linalg.norm(ref)
+        if first is None:
+            first = B
+        assert np.array_equal(B, first)
+    assert bb.bblock_last_launch_count(ctx) > 0
+    # one chunk: the same launches as the device call, so the same bits
+    bb.bblock_set_option(ctx, "host_chunks", 1)
+    B = np.full((n_t, 3, 6, 5, 4), np.nan, np.complex128)
+    bb.bblock_compute_host(ctx, inp.V, *[inp.phi[0][i] for i in range(3)], inp.momenta,
+                           inp.spins, coeffs, B, stream)
+    assert np.array_equal(B, dev_out)
+    with pytest.raises(bb.BblockError):
+        bb.bblock_set_option(ctx, "host_chunks", 65)
+    bb.bblock_destroy(ctx)
+
+
 def test_batch_with_uneven_dilution_matches_single_calls(bb, torch_cuda, form):
     torch = torch_cuda
     dev = torch.device("cuda:0")
