@@ -202,6 +202,11 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 #define BBLOCK_OPT_CORRUPT_CANARY 9  /* test hook (with BBLOCK_OPT_CHECKS): 1 makes the next
                                        call overwrite its first canary from the host, in
                                        stream order between the fill and the check, once */
+#define BBLOCK_OPT_TC_PROJECTION 12  /* mixed forms: 1 runs the projection (Eq. 2) on the
+                                       tensor cores in the form's operand split, accumulated as
+                                       in the contraction; 0 (default): FP32 FMA, which is
+                                       faster at the benchmarked sizes and more accurate. The
+                                       index checks use the FP32 projection */
 #define BBLOCK_OPT_HOST_CHUNKS 11  /* bblock_compute_host: chunks of time slices whose copies
                                        overlap the computation, 1..64 (0, the default: 8). With
                                        1 the blocks equal those of bblock_compute bit for bit;

@@ -43,7 +43,7 @@ EXPORTED = (
 TUNE_FEATURES = 12
 OPTIONS = {"graphs": 1, "tc_nc": 2, "tc_chunk": 3, "slabs": 4, "checks": 5, "wave_mb": 6,
            "wait_limit_us": 7, "fail_next_alloc": 8, "corrupt_canary": 9, "tc_cluster": 10,
-           "host_chunks": 11}
+           "host_chunks": 11, "tc_projection": 12}
 
 
 class BblockError(RuntimeError):

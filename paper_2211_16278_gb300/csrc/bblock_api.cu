@@ -75,6 +75,7 @@ struct bblock_ctx {
   int opt_corrupt_canary = 0; // test hook: the next call overwrites its first canary once
   int opt_tc_cluster = 0;     // tensor-core cluster size: 0 automatic, 1 none, 2 / 4 / 8
   int opt_host_chunks = 0;    // bblock_compute_host chunks of time slices (0: kHostChunks)
+  int opt_tc_proj = 0;        // mixed forms: Eq. 2 on the tensor cores (1) or FP32 FMA (0)
   long long cycles_per_us = 2070;
 };
 
@@ -627,10 +628,37 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       return launch_convert_f32(reinterpret_cast<const F32ConvSeg*>(c->d_tab + sofs),
                                 (int)segs.size(), max_seg, s);
     }));
-    CK(c, timed_launch(c, K_PROJECT, s, [&] {
-      return launch_project_f32(d_fields, (int)fields.size(), rows, n_ev, max_ndf, c->opt_checks,
-                                c->d_dbg, c->d_status, s);
-    }));
+    if (c->opt_checks || !c->opt_tc_proj) {
+      // the FP32 projection (the default, and the checked variant: it checks every index)
+      CK(c, timed_launch(c, K_PROJECT, s, [&] {
+        return launch_project_f32(d_fields, (int)fields.size(), rows, n_ev, max_ndf,
+                                  c->opt_checks, c->d_dbg, c->d_status, s);
+      }));
+    } else {
+      // Eq. 2 on the tensor cores in the form's split, drained every stage; the N tile
+      // with the fewest tiles over the fields (the narrower one on a tie)
+      TcParams pp{};
+      int best_tiles = 0;
+      for (int nc = 16; nc <= 48; nc += 16) {   // the N tiles the kernel accepts
+        int t = 0;
+        for (const ProjFieldF& f : fields) t = std::max(t, (f.nd + nc - 1) / nc);
+        if (best_tiles == 0 || t < best_tiles) { best_tiles = t; pp.NC = nc; }
+      }
+      pp.pfields = d_fields;
+      pp.p_n_fields = (int)fields.size();
+      pp.p_rows = rows;
+      pp.p_n_ev = n_ev;
+      pp.p_m_tiles = (rows + 127) / 128;
+      pp.p_n_tiles = best_tiles;
+      pp.total_units = (long long)fields.size() * pp.p_m_tiles * pp.p_n_tiles;
+      pp.chunk_stages = 1;
+      pp.status = c->d_status;
+      pp.dbg = c->d_dbg;
+      pp.wait_limit = c->opt_wait_us > 0 ? (long long)c->opt_wait_us * c->cycles_per_us
+                                         : 4000000000LL;
+      const int pgrid = (int)std::min<long long>(pp.total_units, c->num_sms);
+      CK(c, timed_launch(c, K_PROJECT, s, [&] { return launch_project_tc(pp, form, pgrid, s); }));
+    }
     TcParams prm{};
     prm.n_jobs = nj;
     prm.total_units = unit;
@@ -941,7 +969,8 @@ std::vector<uint64_t> call_signature(const bblock_ctx* c, const std::vector<JobI
               ((uint64_t)per_mom << 16) | ((uint64_t)c->opt_tc_nc << 24) |
               ((uint64_t)c->opt_tc_chunk << 32) | ((uint64_t)c->opt_slabs << 40));
   k.push_back((uint64_t)n_mom | ((uint64_t)n_spin << 32));
-  k.push_back((uint64_t)wave_budget(c) ^ ((uint64_t)c->opt_tc_cluster << 60));
+  k.push_back((uint64_t)wave_budget(c) ^ ((uint64_t)c->opt_tc_cluster << 60) ^
+              ((uint64_t)c->opt_tc_proj << 56));
   for (int i = 0; i < 3 * n_mom; ++i) k.push_back((uint64_t)(uint32_t)momenta[i]);
   for (int i = 0; i < 3 * n_spin; ++i) k.push_back((uint64_t)(uint32_t)spin_idx[i]);
   const int n_coef = 2 * n_spin * (per_mom ? n_mom : 1);
@@ -1666,6 +1695,10 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) break;
       c->opt_tc_cluster = value;
       return BBLOCK_OK;
+    case BBLOCK_OPT_TC_PROJECTION:
+      if (value != 0 && value != 1) break;
+      c->opt_tc_proj = value;
+      return BBLOCK_OK;
     case BBLOCK_OPT_HOST_CHUNKS:
       if (value < 0 || value > 64) break;
       c->opt_host_chunks = value;
@@ -1695,6 +1728,7 @@ int bblock_get_option(const bblock_ctx* c, int option) {
     case BBLOCK_OPT_CORRUPT_CANARY: return c->opt_corrupt_canary;
     case BBLOCK_OPT_TC_CLUSTER: return c->opt_tc_cluster;
     case BBLOCK_OPT_HOST_CHUNKS: return c->opt_host_chunks;
+    case BBLOCK_OPT_TC_PROJECTION: return c->opt_tc_proj;
     case BBLOCK_OPT_CHECKS: return c->opt_checks;
     default: return BBLOCK_ERR_INVALID_ARG;
   }

@@ -114,6 +114,13 @@ struct TcParams {
   unsigned long long* dbg;
   // limit of every bounded wait, in SM cycles (about 2 s by default; a test hook shortens it)
   long long wait_limit;
+  // projection mode (launch_project_tc): fields of Eq. 2 and their tiling; units are
+  // (128-row tile, field, N tile of NC columns), p_m_tiles x fields x p_n_tiles in all
+  const ProjFieldF* pfields;
+  int p_n_fields;
+  int p_rows;                    // 3 L^3 rows (site, colour) of V
+  int p_n_ev;                    // eigenvectors: the K extent
+  int p_m_tiles, p_n_tiles;
 };
 
 enum TcForm { TC_BF16_3 = 0, TC_BF16_6 = 1, TC_BF16_9 = 2, TC_TF32_3 = 3 };
@@ -132,6 +139,9 @@ cudaError_t launch_project_f32(const ProjFieldF* d_fields, int n_fields, int row
 // cluster: 1 (plain kernel) or 2, 4, 8 CTAs sharing each diquark tile (BF16 forms, no
 // index checks); grid: CTAs wanted, capped at the clusters that fit at once
 cudaError_t launch_contract_tc(const TcParams& p, int form, int cluster, int grid, cudaStream_t s);
+// Eq. 2 for the mixed forms on the tensor cores: every field of p.pfields, in the form's
+// operand split, accumulated as in the contraction; writes each field's FP32 q.
+cudaError_t launch_project_tc(const TcParams& p, int form, int grid, cudaStream_t s);
 int tc_groups_per_stage(int form);
 cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab, int P_total,
                                     long long max_elems, int checks, unsigned long long* dbg,

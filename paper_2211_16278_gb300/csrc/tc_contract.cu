@@ -346,6 +346,23 @@ __device__ __forceinline__ Unit decode_unit(const TcParams& prm, long long u, in
   return w;
 }
 
+// Projection units: (128-row tile, field, N tile), the row tile outermost so that the CTAs
+// running at once share their V tiles in L2; the K sum (eigenvector index l) runs over
+// ceil(N_ev / KS) stages. N tiles past the field's columns are empty.
+__device__ __forceinline__ Unit decode_unit_proj(const TcParams& prm, long long u, int KS) {
+  Unit w;
+  const long long per_row_tile = (long long)prm.p_n_fields * prm.p_n_tiles;
+  w.mt = (int)(u / per_row_tile);
+  const long long r = u - (long long)w.mt * per_row_tile;
+  w.job = (int)(r / prm.p_n_tiles);
+  w.nt = (int)(r - (long long)w.job * prm.p_n_tiles);
+  w.slab = 0;
+  w.x_begin = 0;
+  w.x_end = 0;
+  w.n_stages = w.nt * prm.NC < prm.pfields[w.job].nd ? (prm.p_n_ev + KS - 1) / KS : 0;
+  return w;
+}
+
 // Bounded wait by one thread: gives up after `limit` SM cycles, raising the CTA abort flag
 // and the status bit, or as soon as another role has raised the abort flag. With
 // abort_flag == nullptr only the time limit ends the wait (the MMA thread's final wait for
@@ -365,10 +382,15 @@ __device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t parity,
   }
 }
 
-template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C>
-__global__ void __launch_bounds__(Roles<TF32, C>::kThreads, 1)
-k_contract_tc(const __grid_constant__ TcParams prm) {
+// The body of both tensor-core kernels. PROJ = false: the contraction (diquark x phase x
+// third quark). PROJ = true: the projection of Eq. 2, q[m][n] = sum_l V[l][m] Phi[l][n]
+// with m = (site, colour) and Phi the coefficient-folded phi columns of one field; the same
+// pipeline with the K index of a stage read as the eigenvector index
+// l = stage * 3G + colour * G + group, and the unit's sum written as the FP32 field.
+template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C, bool PROJ>
+__device__ __forceinline__ void tc_body(const TcParams& prm) {
   using R = Roles<TF32, C>;
+  static_assert(!PROJ || (C == 1 && !CHECKS), "the projection runs without clusters or checks");
   constexpr int G = TF32 ? 8 : 16;                 // (site, pair) groups per stage
   // transaction bytes a stage receives from the peers: their diquark rows, every plane
   constexpr uint32_t kPeerTx = (uint32_t)((C - 1) * (R::kARows / 8) * 768 * LEVELS * 2);
@@ -380,6 +402,10 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
   // groups whose loads a producer thread issues together before computing: all 8 in one
   // round where the registers allow it; the cluster and checked variants would spill
   constexpr int kLoadRun = (C == 1 && !CHECKS) ? 8 : 4;
+  auto decode = [&](long long u) -> Unit {
+    if constexpr (PROJ) return decode_unit_proj(prm, u, 3 * G);
+    else return decode_unit(prm, u, G);
+  };
   // piece products (i, j): leading (0, 0) first, then by increasing i + j
   constexpr int PI[9] = {0, 0, 1, 1, 0, 2, 1, 2, 2};
   constexpr int PJ[9] = {0, 1, 0, 1, 2, 0, 2, 1, 2};
@@ -464,12 +490,37 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
     const bool row_used = is_a || (is_b && rr < NC);
     long long s_g = 0;
     for (long long u = u0; u < prm.total_units; u += du) {
-      const Unit w = decode_unit(prm, u, G);
+      const Unit w = decode(u);
+      // per-unit constants of this thread's row
+      bool row_ok = false;
+      int off1 = 0, off2 = 0, s1 = 0, s2 = 0, pidx = 0;
+      const float2* phase_p = nullptr;
+      // projection: the unit's field, read once per unit (A: V column m; B: the folded
+      // phi column n, its terms' rows and FP32 weights)
+      const float2* p_src = nullptr;
+      int p_nd = 0, p_terms = 0;
+      int p_off[kMaxTerms] = {};
+      float2 p_w[kMaxTerms];
+      if constexpr (PROJ) {
+        const ProjFieldF& F = prm.pfields[w.job];
+        p_nd = F.nd;
+        off1 = is_a ? w.mt * kTcM + rr : w.nt * NC + rr;
+        row_ok = is_a ? off1 < prm.p_rows : (row_used && off1 < p_nd);
+        if (is_a) {
+          p_src = F.V + off1;
+        } else {
+          p_src = F.phi + off1;
+          p_terms = F.n_terms;
+#pragma unroll
+          for (int t = 0; t < kMaxTerms; ++t) {
+            p_off[t] = t < p_terms ? F.row_off[t] * p_nd : 0;
+            p_w[t] = t < p_terms ? make_float2((float)F.w[t].x, (float)F.w[t].y)
+                                 : make_float2(0.f, 0.f);
+          }
+        }
+      } else {
       const TcJob& J = prm.jobs[w.job];
       const int nd1 = J.nd1, nd2 = J.nd2, nd3 = J.nd3;
-      // per-unit constants of this thread's row
-      bool row_ok;
-      int off1 = 0, off2 = 0, s1 = 0, s2 = 0, pidx = 0;
       if (is_a) {
         // M side: diquark of the pair m = d1 * nd2 + d2
         const int m = w.mt * kTcM + rr;
@@ -496,7 +547,8 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
       }
       __syncwarp();
       named_bar(kBarProd, R::kProdThreads);
-      const float2* phase_p = prm.phase + (size_t)pidx * prm.X;
+      phase_p = prm.phase + (size_t)pidx * prm.X;
+      }
       for (int st = 0; st < w.n_stages; ++st, ++s_g) {
         const int slot = (int)(s_g % STAGES);
         bool ok = !abort_flag;
@@ -507,6 +559,44 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
         ok = __all_sync(0xffffffffu, ok);
         if (ok && row_used) {
           float re[3][8], im[3][8];
+          if constexpr (PROJ) {
+            // element (colour c, group g0 + j) of this stage is eigenvector index l
+            const int rows = prm.p_rows, n_ev = prm.p_n_ev;
+            if (is_a) {
+              float2 v[3][8];
+#pragma unroll
+              for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const int l = st * 3 * G + c * G + g0 + j;
+                  v[c][j] = (j < NG && row_ok && l < n_ev) ? p_src[(size_t)l * rows]
+                                                           : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+              for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) { re[c][j] = v[c][j].x; im[c][j] = v[c][j].y; }
+            } else {
+#pragma unroll
+              for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const int l = st * 3 * G + c * G + g0 + j;
+                  float2 b = make_float2(0.f, 0.f);
+                  if (j < NG && row_ok && l < n_ev) {
+#pragma unroll
+                    for (int t = 0; t < kMaxTerms; ++t)
+                      if (t < p_terms) {
+                        const float2 f = p_src[(size_t)p_off[t] + (size_t)l * p_nd];
+                        b.x = fmaf(p_w[t].x, f.x, fmaf(-p_w[t].y, f.y, b.x));
+                        b.y = fmaf(p_w[t].x, f.y, fmaf(p_w[t].y, f.x, b.y));
+                      }
+                  }
+                  re[c][j] = b.x;
+                  im[c][j] = b.y;
+                }
+            }
+          } else {
           // first group of this thread's run of NG
           const int gi0 = st * G + g0;
           int xl = gi0 / np, pr = gi0 - xl * np;
@@ -578,6 +668,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
                 re[1][jj] = 0.f; im[1][jj] = 0.f;
                 re[2][jj] = 0.f; im[2][jj] = 0.f;
               }
+          }
           }
           // colour c occupies K bytes [32c, 32c + 32) (BF16; TF32: [32c, 32c + 32) of each
           // 8-group stage as well); group g sits in 16-byte column 2c + g / 8 at 2 (g % 8)
@@ -652,7 +743,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
       long long s_g = 0, c_g = 0;
       bool stop = false;
       for (long long u = u0; u < prm.total_units && !stop; u += du) {
-        const Unit w = decode_unit(prm, u, G);
+        const Unit w = decode(u);
         for (int st = 0; st < w.n_stages; ++st, ++s_g) {
           const int slot = (int)(s_g % STAGES);
           const int buf = (int)(c_g & 1);
@@ -729,8 +820,7 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
     const uint32_t run_r = tmem + lane_base + (uint32_t)(8 * NC);
     long long c_g = 0;
     for (long long u = u0; u < prm.total_units; u += du) {
-      const Unit w = decode_unit(prm, u, G);
-      const TcJob& J = prm.jobs[w.job];
+      const Unit w = decode(u);
       const int n_chunks = (w.n_stages + prm.chunk_stages - 1) / prm.chunk_stages;
       for (int ch = 0; ch < n_chunks; ++ch, ++c_g) {
         const int buf = (int)(c_g & 1);
@@ -760,8 +850,27 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
         named_bar(kBarEpi, kEpiWarps * 32);
         if (tid == 0) mbar_arrive(smem_u32(&bar_acc_empty[buf]));
         __syncwarp();   // tcgen05.ld below is warp-aligned
-        if (ok && ch == n_chunks - 1) {
+        if (PROJ && ok && ch == n_chunks - 1) {
+          // projection unit done: the running sum is the field's tile q[m][n]
+          const ProjFieldF& F = prm.pfields[w.job];
+          const int m = w.mt * kTcM + row, nd = F.nd;
+          for (int col = 0; col < NC; col += 16) {
+            float vr[16], vi[16];
+            __syncwarp();
+            tmem_ld16(run_r + col, vr);
+            tmem_ld16(run_r + NC + col, vi);
+            tmem_wait_ld();
+            if (m < prm.p_rows) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int n = w.nt * NC + col + i;
+                if (n < nd) F.q[(size_t)m * nd + n] = make_float2(vr[i], vi[i]);
+              }
+            }
+          }
+        } else if (!PROJ && ok && ch == n_chunks - 1) {
           // unit done: write the FP32 running sum as this slab's partial block
+          const TcJob& J = prm.jobs[w.job];
           const int m = w.mt * kTcM + row;
           const int M = J.nd1 * J.nd2, nd3 = J.nd3, Ntot = prm.P * nd3;
           for (int col = 0; col < NC; col += 16) {
@@ -802,6 +911,17 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
 }
 
 template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C>
+__global__ void __launch_bounds__(Roles<TF32, C>::kThreads, 1)
+k_contract_tc(const __grid_constant__ TcParams prm) {
+  tc_body<TF32, LEVELS, NPROD, CHECKS, C, false>(prm);
+}
+template <bool TF32, int LEVELS, int NPROD>
+__global__ void __launch_bounds__(Roles<TF32, 1>::kThreads, 1)
+k_project_tc(const __grid_constant__ TcParams prm) {
+  tc_body<TF32, LEVELS, NPROD, false, 1, true>(prm);
+}
+
+template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C>
 cudaError_t launch_variant(const TcParams& prm, int grid, cudaStream_t s) {
   using Lay = TcLayout<TF32, LEVELS>;
   const size_t smem = (size_t)Lay::kStages * Lay::kStageBytes;
@@ -833,6 +953,17 @@ cudaError_t launch_variant(const TcParams& prm, int grid, cudaStream_t s) {
   cfg.gridDim = dim3((unsigned)(C * (want < max_clusters ? want : max_clusters)));
   e = cudaLaunchKernelEx(&cfg, kern, prm);
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <bool TF32, int LEVELS, int NPROD>
+cudaError_t launch_projection(const TcParams& prm, int grid, cudaStream_t s) {
+  using Lay = TcLayout<TF32, LEVELS>;
+  const size_t smem = (size_t)Lay::kStages * Lay::kStageBytes;
+  auto kern = k_project_tc<TF32, LEVELS, NPROD>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, Roles<TF32, 1>::kThreads, smem, s>>>(prm);
   return cudaGetLastError();
 }
 
@@ -883,6 +1014,22 @@ cudaError_t launch_contract_tc(const TcParams& prm, int form, int cluster, int g
     case TC_BF16_6: return launch_form<false, 3, 6>(prm, cluster, grid, s);
     case TC_BF16_9: return launch_form<false, 3, 9>(prm, cluster, grid, s);
     case TC_TF32_3: return launch_form<true, 2, 3>(prm, cluster, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_project_tc(const TcParams& prm, int form, int grid, cudaStream_t s) {
+  if (prm.total_units == 0) return cudaSuccess;
+  if (prm.NC < 16 || prm.NC > kMaxNC || prm.NC % 16 != 0 || prm.chunk_stages < 1 ||
+      prm.checks || !prm.pfields || prm.p_n_fields < 1 || prm.p_rows < 1 || prm.p_n_ev < 1 ||
+      prm.p_m_tiles < 1 || prm.p_n_tiles < 1 ||
+      prm.total_units != (long long)prm.p_m_tiles * prm.p_n_fields * prm.p_n_tiles)
+    return cudaErrorInvalidValue;
+  switch (form) {
+    case TC_BF16_3: return launch_projection<false, 2, 3>(prm, grid, s);
+    case TC_BF16_6: return launch_projection<false, 3, 6>(prm, grid, s);
+    case TC_BF16_9: return launch_projection<false, 3, 9>(prm, grid, s);
+    case TC_TF32_3: return launch_projection<true, 2, 3>(prm, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
