@@ -29,6 +29,12 @@
 // only for wide blocks (13 % at 448 columns with C = 2): the stage time barely falls with
 // the diquark work per CTA. C = 1 is the plain kernel.
 //
+// Projection (k_project_tc, opt-in): the same pipeline computes Eq. 2 for the mixed forms,
+// q[m][n] = sum_l V[l][m] Phi[l][n], with A rows the (site, colour) rows of V, B rows a
+// field's coefficient-folded phi columns, and a stage's K element read as the eigenvector
+// index; each unit writes its FP32 field tile. Measured slower than the FP32 FMA projection
+// at N_ev = 96-264 (the producers wait on V loads), so it is not the default.
+//
 // Warp roles: 0-3 epilogue (TMEM lanes 0-127: drains, partial write-out), 4 MMA issue and
 // TMEM allocation, 5.. operand producers (11 warps for BF16, 6 for TF32). Every wait is
 // bounded; on a timeout the CTA raises an abort flag and a status bit, the roles run out
