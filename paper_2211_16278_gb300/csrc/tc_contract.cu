@@ -9,11 +9,11 @@
 // of 16 (BF16) or 8 (TF32) (site, pair) groups, split each FP32 value into pieces
 // v = v0 + v1 (+ v2) and store them as K-major 8x16-byte core matrices; one thread issues
 // the MMAs. Complex products use separate real and imaginary planes. In the three-piece
-// BF16 forms the third-quark operand is stored as -Bi | Br | Bi, and one complex product is
-// two MMAs of N = 2 NC:
+// BF16 forms and TF32 the third-quark operand is stored as -Bi | Br | Bi, and one complex
+// product is two MMAs of N = 2 NC:
 //   [Cr | Ci] += Ar [Br | Bi],   [Cr | Ci] += Ai [-Bi | Br];
-// the other forms, bound by their producers rather than by the MMAs, skip the -Bi plane and
-// take four MMAs of N = NC (the -Ai Bi product with the B-negate bit).
+// the 2-piece BF16 form, bound by its producers rather than by the MMAs, skips the -Bi
+// plane and takes four MMAs of N = NC (the -Ai Bi product with the B-negate bit).
 // Accuracy: the TMEM accumulator rounds towards zero, so the leading piece product (v0 w0)
 // goes to its own accumulator and is drained every `chunk_stages` stages into an FP32
 // running sum (round to nearest) kept in TMEM; the smaller correction products share a
@@ -84,12 +84,12 @@ constexpr int kBPlaneBytes = kMaxNC * 96;        // room for one plane of up to 
 // product takes two MMAs of N = 2 NC into the adjacent [Cr | Ci] accumulator columns:
 //   [Cr | Ci] += Ar [Br | Bi],   [Cr | Ci] += Ai [-Bi | Br].
 // Each reads the 128-row A tile once, half as often as four N = NC real products would.
-// Measured, this pays where the MMAs bound the stage (three BF16 pieces: 14 % at L = 48).
-// Where the producers bound it (two pieces, TF32) the extra -Bi stores and the larger
-// stages (less L1 for the producers' loads) cost 2-10 %: those forms keep two planes,
-// Br | Bi, and four MMAs of N = NC.
+// Measured, this pays in the three-piece BF16 forms (14 % at L = 48) and in TF32 (3 %).
+// The 2-piece BF16 form, bound by its producers, loses 2-4 % to the extra -Bi stores and
+// the larger stages (less L1 for the producers' loads): it keeps two planes, Br | Bi, and
+// four MMAs of N = NC.
 template <bool TF32, int LEVELS> struct TcLayout {
-  static constexpr bool kTwoMma = !TF32 && LEVELS == 3;
+  static constexpr bool kTwoMma = TF32 || LEVELS == 3;
   static constexpr int kBPlanes = kTwoMma ? 3 : 2;
   static constexpr int kBr = kTwoMma ? 1 : 0, kBi = kBr + 1;   // plane slots; -Bi is slot 0
   static constexpr int kStages = LEVELS == 3 ? 2 : 3;
