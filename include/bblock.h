@@ -57,11 +57,15 @@ extern "C" {
 /* Arithmetic of the projection and the contraction. */
 typedef enum {
   BBLOCK_FP64 = 0,       /* IEEE double throughout (DFMA); parity target 1e-12 */
-  BBLOCK_TF32X3 = 1,     /* tensor-core TF32 split (hi/lo, 3 products), FP32 accumulate */
-  BBLOCK_BF16_SPLIT = 2, /* tensor-core BF16 split (3, 6 or 9 products), FP32 accumulate */
-  BBLOCK_DF64 = 3        /* FP64 projection, contraction in double-float arithmetic (pairs
-                            of FP32, about 48 significant bits) on the FP32 pipe, FP64 slab
-                            reduction; parity target 1e-12 */
+  BBLOCK_TF32X3 = 1,     /* contraction on the tensor cores in a TF32 split (hi/lo, 3
+                            products), FP32 accumulate; projection in FP32 FMA (or on the
+                            tensor cores, BBLOCK_OPT_TC_PROJECTION); parity target 1e-6 */
+  BBLOCK_BF16_SPLIT = 2, /* as BBLOCK_TF32X3 with a BF16 split (3, 6 or 9 products);
+                            parity target 1e-6 with 6 or 9 products */
+  BBLOCK_DF64 = 3        /* projection and contraction in double-float arithmetic (pairs
+                            of FP32, about 48 significant bits) on the FP32 pipe; FP64 only
+                            for the input conversion, the phases and the slab reduction;
+                            parity target 1e-12 */
 } bblock_precision;
 
 typedef struct bblock_ctx bblock_ctx;

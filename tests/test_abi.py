@@ -65,3 +65,23 @@ def test_null_arguments_are_rejected(lib):
     assert lib.bblock_status(None) == -1
     lib.bblock_destroy(None)  # no-op
     assert lib.bblock_last_launch_count(None) == 0
+
+
+def header_defines(prefix):
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2))
+            for m in re.finditer(rf"#define\s+{prefix}(\w+)\s+\(?(-?\d+)\)?", text)}
+
+
+def test_binding_options_and_precisions_match_header():
+    """The binding's option and precision names map to the header's values, one for one."""
+    opts = {k.lower(): v for k, v in header_defines("BBLOCK_OPT_").items()}
+    assert opts == bbm.OPTIONS
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    enum = re.search(r"typedef enum \{([^}]*)\} bblock_precision;", text, re.S).group(1)
+    precisions = {m.group(1).lower(): int(m.group(2))
+                  for m in re.finditer(r"BBLOCK_(\w+)\s*=\s*(\d+)", enum)}
+    assert precisions == {"fp64": 0, "tf32x3": 1, "bf16_split": 2, "df64": 3}
+    for name in ("fp64", "tf32x3", "df64"):
+        assert bbm.PRECISIONS[name] == precisions[name]
+    assert bbm.PRECISIONS["bf16"] == precisions["bf16_split"]
