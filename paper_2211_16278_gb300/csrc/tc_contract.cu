@@ -525,35 +525,35 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
           }
         }
       } else {
-      const TcJob& J = prm.jobs[w.job];
-      const int nd1 = J.nd1, nd2 = J.nd2, nd3 = J.nd3;
-      if (is_a) {
-        // M side: diquark of the pair m = d1 * nd2 + d2
-        const int m = w.mt * kTcM + rr;
-        row_ok = m < nd1 * nd2;
-        const int d1 = row_ok ? m / nd2 : 0, d2 = row_ok ? m - d1 * nd2 : 0;
-        off1 = d1; off2 = d2; s1 = nd1; s2 = nd2;
-      } else {
-        // N side: phase x third quark of the column n = p * nd3 + d3
-        const int n = (w.nt * C + (int)rank) * NC + rr;
-        row_ok = row_used && n < prm.P * nd3;
-        const int p = row_ok ? n / nd3 : 0, d3 = row_ok ? n - p * nd3 : 0;
-        off1 = d3; s1 = nd3; pidx = p;
-      }
-      // Producer warps run their stages independently; at a unit boundary they meet twice:
-      // once so that no warp still reads the previous unit's pointer table while it is
-      // rewritten, once to publish the new table. (bar.sync is warp-aligned: reconverge
-      // every warp before it.)
-      __syncwarp();
-      named_bar(kBarProd, R::kProdThreads);
-      if (pt < np) {
-        s_q1[pt] = J.q1[prm.a_slot[pt]];
-        s_q2[pt] = J.q2[prm.b_slot[pt]];
-        s_q3[pt] = J.q3[pt];
-      }
-      __syncwarp();
-      named_bar(kBarProd, R::kProdThreads);
-      phase_p = prm.phase + (size_t)pidx * prm.X;
+        const TcJob& J = prm.jobs[w.job];
+        const int nd1 = J.nd1, nd2 = J.nd2, nd3 = J.nd3;
+        if (is_a) {
+          // M side: diquark of the pair m = d1 * nd2 + d2
+          const int m = w.mt * kTcM + rr;
+          row_ok = m < nd1 * nd2;
+          const int d1 = row_ok ? m / nd2 : 0, d2 = row_ok ? m - d1 * nd2 : 0;
+          off1 = d1; off2 = d2; s1 = nd1; s2 = nd2;
+        } else {
+          // N side: phase x third quark of the column n = p * nd3 + d3
+          const int n = (w.nt * C + (int)rank) * NC + rr;
+          row_ok = row_used && n < prm.P * nd3;
+          const int p = row_ok ? n / nd3 : 0, d3 = row_ok ? n - p * nd3 : 0;
+          off1 = d3; s1 = nd3; pidx = p;
+        }
+        // Producer warps run their stages independently; at a unit boundary they meet twice:
+        // once so that no warp still reads the previous unit's pointer table while it is
+        // rewritten, once to publish the new table. (bar.sync is warp-aligned: reconverge
+        // every warp before it.)
+        __syncwarp();
+        named_bar(kBarProd, R::kProdThreads);
+        if (pt < np) {
+          s_q1[pt] = J.q1[prm.a_slot[pt]];
+          s_q2[pt] = J.q2[prm.b_slot[pt]];
+          s_q3[pt] = J.q3[pt];
+        }
+        __syncwarp();
+        named_bar(kBarProd, R::kProdThreads);
+        phase_p = prm.phase + (size_t)pidx * prm.X;
       }
       for (int st = 0; st < w.n_stages; ++st, ++s_g) {
         const int slot = (int)(s_g % STAGES);
@@ -603,78 +603,78 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                 }
             }
           } else {
-          // first group of this thread's run of NG
-          const int gi0 = st * G + g0;
-          int xl = gi0 / np, pr = gi0 - xl * np;
-          uint32_t vmask = 0;   // groups of this run that lie inside the slab and a used row
+            // first group of this thread's run of NG
+            const int gi0 = st * G + g0;
+            int xl = gi0 / np, pr = gi0 - xl * np;
+            uint32_t vmask = 0;   // groups of this run that lie inside the slab and a used row
 #pragma unroll
-          for (int half = 0; half < 8 / kLoadRun; ++half) {
-            if (half * kLoadRun >= NG) break;
-            // kLoadRun groups: issue every load first, then compute
-            float2 ld[kLoadRun][6];
-            bool vld[kLoadRun];
+            for (int half = 0; half < 8 / kLoadRun; ++half) {
+              if (half * kLoadRun >= NG) break;
+              // kLoadRun groups: issue every load first, then compute
+              float2 ld[kLoadRun][6];
+              bool vld[kLoadRun];
 #pragma unroll
-            for (int j = 0; j < kLoadRun; ++j) {
-              if (half * kLoadRun + j >= NG) break;
-              const int x = w.x_begin + xl;
-              vld[j] = row_ok && x < w.x_end;
-              int xs = vld[j] ? x : w.x_begin;
-              if (CHECKS) {
-                const long long fl = 3LL * prm.X * s1;            // elements of a field
-                bool good = idx_ok(prm, (long long)xs * 3 * s1 + off1 + 2LL * s1, fl, is_a ? 1 : 3, w.job) &&
-                            idx_ok(prm, pr, np, 6, w.job);
-                if (is_a) good = good && idx_ok(prm, (long long)xs * 3 * s2 + off2 + 2LL * s2, 3LL * prm.X * s2, 2, w.job);
-                else good = good && idx_ok(prm, (long long)pidx * prm.X + xs, (long long)prm.P * prm.X, 4, w.job);
-                if (!good) { vld[j] = false; xs = 0; pr = 0; }
+              for (int j = 0; j < kLoadRun; ++j) {
+                if (half * kLoadRun + j >= NG) break;
+                const int x = w.x_begin + xl;
+                vld[j] = row_ok && x < w.x_end;
+                int xs = vld[j] ? x : w.x_begin;
+                if (CHECKS) {
+                  const long long fl = 3LL * prm.X * s1;            // elements of a field
+                  bool good = idx_ok(prm, (long long)xs * 3 * s1 + off1 + 2LL * s1, fl, is_a ? 1 : 3, w.job) &&
+                              idx_ok(prm, pr, np, 6, w.job);
+                  if (is_a) good = good && idx_ok(prm, (long long)xs * 3 * s2 + off2 + 2LL * s2, 3LL * prm.X * s2, 2, w.job);
+                  else good = good && idx_ok(prm, (long long)pidx * prm.X + xs, (long long)prm.P * prm.X, 4, w.job);
+                  if (!good) { vld[j] = false; xs = 0; pr = 0; }
+                }
+                if (is_a) {
+                  const float2* uq = s_q1[pr] + (size_t)xs * 3 * s1 + off1;
+                  const float2* vq = s_q2[pr] + (size_t)xs * 3 * s2 + off2;
+                  ld[j][0] = uq[0]; ld[j][1] = uq[s1]; ld[j][2] = uq[2 * s1];
+                  ld[j][3] = vq[0]; ld[j][4] = vq[s2]; ld[j][5] = vq[2 * s2];
+                } else {
+                  const float2* q = s_q3[pr] + (size_t)xs * 3 * s1 + off1;
+                  ld[j][0] = q[0]; ld[j][1] = q[s1]; ld[j][2] = q[2 * s1];
+                  ld[j][3] = phase_p[xs];
+                }
+                if (++pr == np) { pr = 0; ++xl; }
               }
-              if (is_a) {
-                const float2* uq = s_q1[pr] + (size_t)xs * 3 * s1 + off1;
-                const float2* vq = s_q2[pr] + (size_t)xs * 3 * s2 + off2;
-                ld[j][0] = uq[0]; ld[j][1] = uq[s1]; ld[j][2] = uq[2 * s1];
-                ld[j][3] = vq[0]; ld[j][4] = vq[s2]; ld[j][5] = vq[2 * s2];
-              } else {
-                const float2* q = s_q3[pr] + (size_t)xs * 3 * s1 + off1;
-                ld[j][0] = q[0]; ld[j][1] = q[s1]; ld[j][2] = q[2 * s1];
-                ld[j][3] = phase_p[xs];
+#pragma unroll
+              for (int j = 0; j < kLoadRun; ++j) {
+                if (half * kLoadRun + j >= NG) break;
+                float2 c0, c1, c2;
+                if (is_a) {
+                  const float2 u0 = ld[j][0], u1 = ld[j][1], u2 = ld[j][2];
+                  const float2 v0 = ld[j][3], v1 = ld[j][4], v2 = ld[j][5];
+                  const float2 a12 = cmulf(u1, v2), a21 = cmulf(u2, v1);
+                  const float2 a20 = cmulf(u2, v0), a02 = cmulf(u0, v2);
+                  const float2 a01 = cmulf(u0, v1), a10 = cmulf(u1, v0);
+                  c0 = make_float2(a12.x - a21.x, a12.y - a21.y);
+                  c1 = make_float2(a20.x - a02.x, a20.y - a02.y);
+                  c2 = make_float2(a01.x - a10.x, a01.y - a10.y);
+                } else {
+                  c0 = cmulf(ld[j][3], ld[j][0]);
+                  c1 = cmulf(ld[j][3], ld[j][1]);
+                  c2 = cmulf(ld[j][3], ld[j][2]);
+                }
+                const int jj = half * kLoadRun + j;
+                vmask |= (uint32_t)vld[j] << jj;
+                re[0][jj] = c0.x; im[0][jj] = c0.y;
+                re[1][jj] = c1.x; im[1][jj] = c1.y;
+                re[2][jj] = c2.x; im[2][jj] = c2.y;
               }
-              if (++pr == np) { pr = 0; ++xl; }
             }
+            // groups past the slab's end or of an unused row (their loads read a valid site)
+            // contribute zeros; this branch is taken only at ragged edges
+            if (vmask != (1u << NG) - 1u) {
 #pragma unroll
-            for (int j = 0; j < kLoadRun; ++j) {
-              if (half * kLoadRun + j >= NG) break;
-              float2 c0, c1, c2;
-              if (is_a) {
-                const float2 u0 = ld[j][0], u1 = ld[j][1], u2 = ld[j][2];
-                const float2 v0 = ld[j][3], v1 = ld[j][4], v2 = ld[j][5];
-                const float2 a12 = cmulf(u1, v2), a21 = cmulf(u2, v1);
-                const float2 a20 = cmulf(u2, v0), a02 = cmulf(u0, v2);
-                const float2 a01 = cmulf(u0, v1), a10 = cmulf(u1, v0);
-                c0 = make_float2(a12.x - a21.x, a12.y - a21.y);
-                c1 = make_float2(a20.x - a02.x, a20.y - a02.y);
-                c2 = make_float2(a01.x - a10.x, a01.y - a10.y);
-              } else {
-                c0 = cmulf(ld[j][3], ld[j][0]);
-                c1 = cmulf(ld[j][3], ld[j][1]);
-                c2 = cmulf(ld[j][3], ld[j][2]);
-              }
-              const int jj = half * kLoadRun + j;
-              vmask |= (uint32_t)vld[j] << jj;
-              re[0][jj] = c0.x; im[0][jj] = c0.y;
-              re[1][jj] = c1.x; im[1][jj] = c1.y;
-              re[2][jj] = c2.x; im[2][jj] = c2.y;
+              for (int jj = 0; jj < 8; ++jj)
+                if (!((vmask >> jj) & 1u)) {
+                  re[0][jj] = 0.f; im[0][jj] = 0.f;
+                  re[1][jj] = 0.f; im[1][jj] = 0.f;
+                  re[2][jj] = 0.f; im[2][jj] = 0.f;
+                }
             }
-          }
-          // groups past the slab's end or of an unused row (their loads read a valid site)
-          // contribute zeros; this branch is taken only at ragged edges
-          if (vmask != (1u << NG) - 1u) {
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj)
-              if (!((vmask >> jj) & 1u)) {
-                re[0][jj] = 0.f; im[0][jj] = 0.f;
-                re[1][jj] = 0.f; im[1][jj] = 0.f;
-                re[2][jj] = 0.f; im[2][jj] = 0.f;
-              }
-          }
           }
           // colour c occupies K bytes [32c, 32c + 32) (BF16; TF32: [32c, 32c + 32) of each
           // 8-group stage as well); group g sits in 16-byte column 2c + g / 8 at 2 (g % 8)
