@@ -62,10 +62,17 @@ typedef enum {
                             tensor cores, BBLOCK_OPT_TC_PROJECTION); parity target 1e-6 */
   BBLOCK_BF16_SPLIT = 2, /* as BBLOCK_TF32X3 with a BF16 split (3, 6 or 9 products);
                             parity target 1e-6 with 6 or 9 products */
-  BBLOCK_DF64 = 3        /* projection and contraction in double-float arithmetic (pairs
+  BBLOCK_DF64 = 3,       /* projection and contraction in double-float arithmetic (pairs
                             of FP32, about 48 significant bits) on the FP32 pipe; FP64 only
                             for the input conversion, the phases and the slab reduction;
                             parity target 1e-12 */
+  BBLOCK_FP16X3 = 4      /* contraction on the tensor cores with FP16 operands split in two
+                            (hi = rn16(v), lo = rn16(v - hi), about 22 bits), 3 products
+                            (hi hi, hi lo, lo hi), FP32 accumulate; the operands are scaled
+                            by powers of two chosen per job from the largest field entry of
+                            each quark line, so FP16's range never overflows, and the FP64
+                            slab reduction removes the scale exactly; projection in FP32 FMA;
+                            parity target 1e-6 */
 } bblock_precision;
 
 typedef struct bblock_ctx bblock_ctx;
@@ -174,6 +181,11 @@ size_t bblock_workspace_bytes(const bblock_ctx* ctx);
 /* Number of kernel launches enqueued by the last compute call. */
 int bblock_last_launch_count(const bblock_ctx* ctx);
 
+/* Number of waves the last compute call ran its jobs in: jobs are taken in list order, and
+ * a wave holds as many as the workspace budget (BBLOCK_OPT_WAVE_MB) allows. 0 for a call
+ * with no work or a NULL context. */
+int bblock_last_wave_count(const bblock_ctx* ctx);
+
 /* Options of a context (bblock_set_option). The tuning options are the search space of
  * the tile autotuner; 0 means "chosen automatically". */
 #define BBLOCK_OPT_GRAPHS 1    /* 1 (default): a call repeated with identical arguments on a
@@ -235,8 +247,12 @@ typedef struct {
   double total_ms;  /* summed event-to-event durations of those launches */
 } bblock_kernel_stat;
 
-/* Turn launch timing on (enable != 0) or off. Off by default. While it is on, calls are
- * not captured into or replayed from CUDA graphs. */
+/* Turn launch timing on (enable != 0) or off. Off by default. Every kernel launch is
+ * bracketed by CUDA events on the launching stream. A call captured into a CUDA graph while
+ * timing is on carries those events as event-record nodes, so graph replays are timed per
+ * launch as well (each replay's times are read before the next replay starts, which waits
+ * for the previous replay to finish). Turning timing on or off changes the call signature:
+ * the next two identical calls run plainly and then capture a new graph. */
 int bblock_profile_enable(bblock_ctx* ctx, int enable);
 
 /* Synchronise the recorded events, write up to max_entries per-kernel totals to
@@ -305,9 +321,11 @@ int bblock_costmodel_predict(bblock_costmodel* model, const float* X, int n, flo
  *
  * It computes the same blocks as bblock_compute for one time slice, but from fields that
  * are already reconstructed, and needs no context:
- *   q1, q2, q3  complex128 [4][L^3][3][nd_i], device memory of the CURRENT device,
- *               q_i[alpha][x][a][d] as in Eq. (2) (spins a caller does not use may hold
- *               anything; they are not read);
+ *   q1, q2, q3  complex128 [4][L^3][3][nd_i], device memory of the CURRENT device: the
+ *               reconstructed field of quark line i, indexed [spin][site][colour][dilution
+ *               index], last index fastest (the fields bblock_compute builds internally
+ *               from V and phi_i); spins a caller does not use may hold anything, they are
+ *               not read;
  *   B_out       complex128 [n_mom][nd1][nd2][nd3], device memory of the current device;
  *   momenta, spin_idx, spin_coeffs: host arrays as for bblock_compute, with one
  *               coefficient per spin triple (no per-momentum coefficients);
@@ -319,7 +337,9 @@ int bblock_costmodel_predict(bblock_costmodel* model, const float* X, int n, flo
  * BBLOCK_NOALLOC_SCRATCH_BYTES that every device loading the library holds until the
  * process exits. It calls no cudaMalloc, cudaFree or other allocating routine. The
  * first call on a device looks up that array's device address (cudaGetSymbolAddress,
- * with the device current); make that first call before any stream capture. All calls
+ * with the device current); make that first call before any stream capture. The address
+ * is kept per device and CUDA context: after a cudaDeviceReset the next call looks it up
+ * again in the new context (make that call, too, before any capture). All calls
  * share the one array and every call overwrites the part it reads, so calls that overlap
  * on the GPU (different streams or host threads without ordering between them) race and
  * must be serialised by the caller. */

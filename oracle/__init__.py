@@ -41,11 +41,14 @@ _lib = None
 
 
 def build(force: bool = False, src: str = _SRC, out: str = _LIB_PATH) -> str:
-    """Compile the C oracle (gcc, -O2, OpenMP) into ``out``; default ``oracle/_build/liboracle.so``."""
+    """Compile the C oracle (gcc, -O3, OpenMP) into ``out``; default ``oracle/_build/liboracle.so``.
+
+    No ``-march=native``: the same source must build and give the same results on the
+    x86-64 development host and the Arm (Grace) GPU host."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", src, "-o", tmp, "-lm"]
+        cmd = ["gcc", "-O3", "-std=c99", "-fopenmp", "-fPIC", "-shared", src, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, out)
     return out
@@ -58,6 +61,7 @@ def load_library(path: str):
     i = ctypes.c_int
     l = ctypes.c_long
     lib.oracle_num_threads.restype = i
+    lib.oracle_set_num_threads.argtypes = [i]
     lib.oracle_phase_table.argtypes = [i, i, P, P]
     lib.oracle_reconstruct.argtypes = [l, i, P, P, i, i, P]
     sig = [i, P, i, P, i, P, i, i, P, i, P, P, i, P]
@@ -87,6 +91,11 @@ def _ptr(a):
 
 def num_threads() -> int:
     return _load().oracle_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on (a timing control only)."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def _spin_args(spin, coef, n_mom):

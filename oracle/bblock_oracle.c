@@ -49,6 +49,15 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* Threads of the following OpenMP loops (n >= 1); a timing control, no arithmetic. */
+void oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* The six nonzero entries of eps_{abc}: (a, b, c, sign). */
 static const int EPS_PERM[6][4] = {
     {0, 1, 2, +1}, {1, 2, 0, +1}, {2, 0, 1, +1},

@@ -27,13 +27,13 @@ ERRORS = {
     -6: "BBLOCK_ERR_DEVICE_FLAG",
     -7: "BBLOCK_ERR_TOO_LARGE",
 }
-PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16": 2, "df64": 3}
+PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16": 2, "df64": 3, "fp16x3": 4}
 
 # Every symbol include/bblock.h declares.
 EXPORTED = (
     "bblock_create", "bblock_destroy", "bblock_last_error", "bblock_status", "bblock_compute",
     "bblock_compute_host", "bblock_compute_batch", "bblock_workspace_bytes",
-    "bblock_last_launch_count", "bblock_profile_enable", "bblock_profile_read",
+    "bblock_last_launch_count", "bblock_last_wave_count", "bblock_profile_enable", "bblock_profile_read",
     "bblock_contract_noalloc", "bblock_set_option", "bblock_get_option", "bblock_autotune",
     "bblock_costmodel_create", "bblock_costmodel_destroy", "bblock_costmodel_num_params",
     "bblock_costmodel_get_params", "bblock_costmodel_set_params", "bblock_costmodel_gradient",
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bblock_workspace_bytes.restype = ctypes.c_size_t
     lib.bblock_last_launch_count.argtypes = [P]
     lib.bblock_last_launch_count.restype = I
+    lib.bblock_last_wave_count.argtypes = [P]
+    lib.bblock_last_wave_count.restype = I
     lib.bblock_profile_enable.argtypes = [P, I]
     lib.bblock_profile_enable.restype = I
     lib.bblock_profile_read.argtypes = [P, ctypes.POINTER(bblock_kernel_stat), I,
@@ -196,6 +198,10 @@ def bblock_workspace_bytes(ctx: Context) -> int:
 
 def bblock_last_launch_count(ctx: Context) -> int:
     return int(load().bblock_last_launch_count(ctx.handle))
+
+
+def bblock_last_wave_count(ctx: Context) -> int:
+    return int(load().bblock_last_wave_count(ctx.handle))
 
 
 def bblock_set_option(ctx: Context, option: str, value: int) -> None:

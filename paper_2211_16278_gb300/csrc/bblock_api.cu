@@ -48,12 +48,20 @@ struct bblock_ctx {
   char* d_tri = nullptr;
   size_t tri_cap = 0;
   int last_launches = 0;
+  int last_waves = 0;         // waves of jobs the last compute call ran in
   size_t ws_budget = 0;
   // launch timing (bblock_profile_enable)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   struct Timed { int kind; cudaEvent_t a, b; };
   std::vector<Timed> timed;
+  // launch timing of CUDA-graph replays: event pairs captured as event-record nodes of the
+  // graph (owned while the graph lives); a replay re-records them, so their times are
+  // harvested into graph_ms / graph_cnt before the next replay or at bblock_profile_read
+  std::vector<Timed> graph_timed;
+  bool graph_pending = false;
+  double graph_ms[8] = {};
+  int graph_cnt[8] = {};
   // options (bblock_set_option)
   int opt_graphs = 1, opt_tc_nc = 0, opt_tc_chunk = 0, opt_slabs = 0, opt_checks = 0;
   unsigned long long* d_dbg = nullptr;  // first index violation of a checked launch
@@ -62,6 +70,7 @@ struct bblock_ctx {
   std::vector<uint64_t> last_sig, graph_sig;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_launches = 0;
+  int graph_waves = 0;
   bool capturing = false;
   // pinned staging that a captured graph's table copies read at every replay: each upload
   // of the captured call (one per wave) keeps its own slot, at graph_tab_off onwards
@@ -85,6 +94,7 @@ constexpr int kHostChunks = 8;
 enum KernelKind { K_PHASE = 0, K_PROJECT, K_CONTRACT, K_REDUCE, K_CONVERT, K_CANARY, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"phase", "project", "contract", "reduce", "convert",
                                            "canary"};
+static_assert(K_COUNT <= 8, "graph launch-time slots");
 
 cudaEvent_t take_event(bblock_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -97,25 +107,59 @@ cudaEvent_t take_event(bblock_ctx* c) {
   return e;
 }
 
-// Enqueue `launch` on `s`; when timing is on, bracket it with events.
+// Enqueue `launch` on `s`; when timing is on, bracket it with events. Under stream capture
+// the events become event-record nodes of the graph (cudaEventRecordExternal), so every
+// replay times its launches too.
 template <class F>
 cudaError_t timed_launch(bblock_ctx* c, int kind, cudaStream_t s, F&& launch) {
   cudaEvent_t a = nullptr, b = nullptr;
-  if (c->prof && !c->capturing) {
+  const unsigned rec_flags = c->capturing ? cudaEventRecordExternal : 0u;
+  if (c->prof) {
     a = take_event(c);
     b = take_event(c);
-    if (a && b) cudaEventRecord(a, s);
+    if (a && b && cudaEventRecordWithFlags(a, s, rec_flags) != cudaSuccess) {
+      cudaGetLastError();
+      c->ev_pool.push_back(a);
+      c->ev_pool.push_back(b);
+      a = b = nullptr;
+    }
   }
   cudaError_t e = launch();
   c->last_launches++;
   if (a && b) {
-    cudaEventRecord(b, s);
-    c->timed.push_back({kind, a, b});
+    if (cudaEventRecordWithFlags(b, s, rec_flags) == cudaSuccess) {
+      (c->capturing ? c->graph_timed : c->timed).push_back({kind, a, b});
+    } else {
+      cudaGetLastError();
+      c->ev_pool.push_back(a);
+      c->ev_pool.push_back(b);
+    }
   } else {
     if (a) c->ev_pool.push_back(a);
     if (b) c->ev_pool.push_back(b);
   }
   return e;
+}
+
+// Add the launch times of the last graph replay (if not yet read) to graph_ms / graph_cnt.
+// Waits for that replay to finish.
+cudaError_t harvest_graph_times(bblock_ctx* c) {
+  if (!c->graph_pending) return cudaSuccess;
+  c->graph_pending = false;
+  cudaError_t rc = cudaSuccess;
+  for (const auto& t : c->graph_timed) {
+    float m = 0.f;
+    cudaError_t e = cudaEventSynchronize(t.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m, t.a, t.b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (rc == cudaSuccess) rc = e;
+      continue;
+    }
+    c->graph_ms[t.kind] += m;
+    c->graph_cnt[t.kind] += 1;
+  }
+  return rc;
 }
 }  // namespace
 
@@ -153,9 +197,16 @@ bool fp64_like(const bblock_config& cfg) {
 size_t wave_budget(const bblock_ctx* c) { return c->opt_wave_bytes ? c->opt_wave_bytes : c->ws_budget; }
 
 void drop_graph(bblock_ctx* c) {
+  // the last replay's launch times are kept; its events then go back to the pool
+  if (c->graph_pending && harvest_graph_times(c) != cudaSuccess) cudaGetLastError();
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
   c->graph_sig.clear();
+  for (const auto& t : c->graph_timed) {
+    c->ev_pool.push_back(t.a);
+    c->ev_pool.push_back(t.b);
+  }
+  c->graph_timed.clear();
 }
 
 int grow_device(bblock_ctx* c, char** p, size_t* cap, size_t need) {
@@ -396,6 +447,7 @@ int validate_job(bblock_ctx* c, const JobIn& j, int idx, bool device, int n_mom 
 
 int tc_form_of(const bblock_config& cfg) {
   if (cfg.precision == BBLOCK_TF32X3) return TC_TF32_3;
+  if (cfg.precision == BBLOCK_FP16X3) return TC_F16_3;
   return cfg.bf16_products == 3 ? TC_BF16_3 : cfg.bf16_products == 9 ? TC_BF16_9 : TC_BF16_6;
 }
 
@@ -419,8 +471,8 @@ struct TcTiling {
 // work per CTA.
 TcTiling choose_tc_tiling(const bblock_ctx* c, const std::vector<JobIn>& jobs, size_t b,
                           size_t e, int P, int form, int nc_fixed) {
-  const bool can_cluster = form != TC_TF32_3 && !c->opt_checks && c->opt_wait_us == 0 &&
-                           c->opt_tc_cluster != 1;
+  const bool can_cluster = form != TC_TF32_3 && form != TC_F16_3 && !c->opt_checks &&
+                           c->opt_wait_us == 0 && c->opt_tc_cluster != 1;
   TcTiling best;
   best.nc = nc_fixed > 0 ? nc_fixed : 48;
   if (nc_fixed <= 0) {
@@ -477,6 +529,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       need += b;
       ++end;
     }
+    ++c->last_waves;
     const int nj = (int)(end - job_idx);
     const TcTiling tt = choose_tc_tiling(c, jobs, job_idx, end, P_launch, form, c->opt_tc_nc);
     const int NC = tt.nc, CL = tt.cluster;
@@ -494,17 +547,21 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
                                    : std::max(min_slabs, choose_slabs(tiles, grid_cap / CL, X, 1, max_slabs));
     int sites_per_slab = (X + n_slab - 1) / n_slab;
     n_slab = (X + sites_per_slab - 1) / sites_per_slab;
-    size_t ws_need = 0;
+    // FP16 form: three per-line maxima per job (the operand scales), at the wave's start
+    const bool amax_on = tc_form_needs_amax(form);
+    const size_t amax_bytes = amax_on ? align_up((size_t)3 * nj * sizeof(uint32_t), 256) : 0;
+    size_t ws_need = amax_bytes;
     for (size_t k = job_idx; k < end; ++k) ws_need += job_bytes(jobs[k], n_slab);
     rc = grow_device(c, &c->d_ws, &c->ws_cap, ws_need);
     if (rc) return rc;
+    uint32_t* d_amax = amax_on ? reinterpret_cast<uint32_t*>(c->d_ws) : nullptr;
 
     std::vector<ProjFieldF> fields;
     std::vector<std::vector<TcJob>> tjobs(sp.n_coef_sets, std::vector<TcJob>(nj));
     std::vector<uint32_t*> canaries;
     std::vector<F32ConvSeg> segs;
     long long max_seg = 0;
-    char* ws = c->d_ws;
+    char* ws = c->d_ws + amax_bytes;
     long long unit = 0;
     for (int k = 0; k < nj; ++k) {
       const JobIn& j = jobs[job_idx + k];
@@ -530,11 +587,12 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       base += in_bytes(j);
       canary(base);
       auto add_field = [&](const float2* phi, int nd, int n_terms, const int* offs,
-                           const double2* w) -> float2* {
+                           const double2* w, int line) -> float2* {
         ProjFieldF f{};
         f.V = Vf;
         f.phi = phi;
         f.q = reinterpret_cast<float2*>(base);
+        f.amax = d_amax ? d_amax + 3 * k + line : nullptr;
         f.nd = nd;
         f.n_terms = n_terms;
         for (int t = 0; t < n_terms; ++t) { f.row_off[t] = offs[t]; f.w[t] = w[t]; }
@@ -548,11 +606,11 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       const float2* q2[4] = {};
       for (int sl = 0; sl < sp.n1; ++sl) {
         int off = sp.alpha_of1[sl] * n_ev;
-        q1[sl] = add_field(phif[0], j.nd[0], 1, &off, &one);
+        q1[sl] = add_field(phif[0], j.nd[0], 1, &off, &one, 0);
       }
       for (int sl = 0; sl < sp.n2; ++sl) {
         int off = sp.beta_of2[sl] * n_ev;
-        q2[sl] = add_field(phif[1], j.nd[1], 1, &off, &one);
+        q2[sl] = add_field(phif[1], j.nd[1], 1, &off, &one, 1);
       }
       std::vector<std::vector<const float2*>> q3(sp.n_coef_sets, std::vector<const float2*>(sp.n_pairs));
       for (int set = 0; set < sp.n_coef_sets; ++set)
@@ -562,7 +620,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
           int offs[kMaxTerms];
           double2 w[kMaxTerms];
           for (size_t t = 0; t < tlist.size(); ++t) { offs[t] = tlist[t].first * n_ev; w[t] = tlist[t].second; }
-          q3[set][pr] = add_field(phif[2], j.nd[2], (int)tlist.size(), offs, w);
+          q3[set][pr] = add_field(phif[2], j.nd[2], (int)tlist.size(), offs, w, 2);
         }
       base = c->d_ws + align_up((size_t)(base - c->d_ws), 256);
       float2* partial = reinterpret_cast<float2*>(base);
@@ -576,6 +634,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
         TcJob& tj = tjobs[set][k];
         for (int i = 0; i < 4; ++i) { tj.q1[i] = q1[i]; tj.q2[i] = q2[i]; }
         for (int pr = 0; pr < sp.n_pairs; ++pr) tj.q3[pr] = q3[set][pr];
+        tj.amax = d_amax ? d_amax + 3 * k : nullptr;
         tj.partial = partial;
         // per-momentum coefficient sets run one momentum per launch into their slice of B
         tj.B = j.B + (per_mom ? (size_t)set * j.nd[0] * j.nd[1] * j.nd[2] : 0);
@@ -628,7 +687,9 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       return launch_convert_f32(reinterpret_cast<const F32ConvSeg*>(c->d_tab + sofs),
                                 (int)segs.size(), max_seg, s);
     }));
-    if (c->opt_checks || !c->opt_tc_proj) {
+    if (amax_on) CK(c, cudaMemsetAsync(d_amax, 0, (size_t)3 * nj * sizeof(uint32_t), s));
+    // the FP16 form takes its operand scales from the FP32 projection's field maxima
+    if (c->opt_checks || !c->opt_tc_proj || amax_on) {
       // the FP32 projection (the default, and the checked variant: it checks every index)
       CK(c, timed_launch(c, K_PROJECT, s, [&] {
         return launch_project_f32(d_fields, (int)fields.size(), rows, n_ev, max_ndf,
@@ -702,6 +763,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
              const int32_t* spin_idx, const double* coeffs, int n_spin, int per_mom,
              cudaStream_t s) {
   c->last_launches = 0;
+  c->last_waves = 0;
   c->last_stream = s;
   c->call_tab_bytes = 0;
   if (jobs.empty() || n_mom == 0) return BBLOCK_OK;
@@ -717,7 +779,8 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
 
   const int X = c->X, rows = c->rows, n_ev = c->cfg.n_ev;
   const int n3_fields = sp.n_pairs * sp.n_coef_sets;
-  const int P_launch = per_mom ? 1 : std::min(n_mom, kMaxPGroup);
+  const int P_launch =
+      per_mom ? 1 : p_group_size(n_mom, c->cfg.precision == BBLOCK_DF64 ? kMaxPGroupDf : kMaxPGroup);
   const int xc = fp64_sites_per_chunk(sp.n_pairs);
   const Fp64Tile tl = fp64_tile_for(P_launch);  // one tile shape for every momentum group
   const int ctas = fp64_contract_ctas_per_sm(P_launch, tl.rn, sp.n_pairs) * c->num_sms;
@@ -749,6 +812,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       need += b;
       ++end;
     }
+    ++c->last_waves;
     const int nj = (int)(end - job_idx);
     long long tiles = 0;
     int max_nd3 = 0, max_ndf = 0;
@@ -938,8 +1002,9 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       }
     } else {
       prm.jobs = reinterpret_cast<const ContractJob*>(c->d_tab + fbytes);
-      for (int p0 = 0; p0 < n_mom; p0 += kMaxPGroup) {
-        const int Pg = std::min(kMaxPGroup, n_mom - p0);
+      const int pg = P_launch;
+      for (int p0 = 0; p0 < n_mom; p0 += pg) {
+        const int Pg = std::min(pg, n_mom - p0);
         prm.p0 = p0;
         CK(c, timed_launch(c, K_CONTRACT, s, [&] {
           return df ? launch_contract_df(prm, Pg, tl.rn, grid, s) : launch_contract_fp64(prm, Pg, tl.rn, grid, s);
@@ -970,7 +1035,7 @@ std::vector<uint64_t> call_signature(const bblock_ctx* c, const std::vector<JobI
               ((uint64_t)c->opt_tc_chunk << 32) | ((uint64_t)c->opt_slabs << 40));
   k.push_back((uint64_t)n_mom | ((uint64_t)n_spin << 32));
   k.push_back((uint64_t)wave_budget(c) ^ ((uint64_t)c->opt_tc_cluster << 60) ^
-              ((uint64_t)c->opt_tc_proj << 56));
+              ((uint64_t)c->opt_tc_proj << 56) ^ ((uint64_t)c->prof << 52));
   for (int i = 0; i < 3 * n_mom; ++i) k.push_back((uint64_t)(uint32_t)momenta[i]);
   for (int i = 0; i < 3 * n_spin; ++i) k.push_back((uint64_t)(uint32_t)spin_idx[i]);
   const int n_coef = 2 * n_spin * (per_mom ? n_mom : 1);
@@ -995,7 +1060,7 @@ int run_jobs_cached(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t
                     int per_mom, cudaStream_t s) {
   // the legacy and per-thread default streams cannot be captured
   const bool capturable = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
-  if (!c->opt_graphs || c->prof || !capturable || jobs.empty() || n_mom == 0)
+  if (!c->opt_graphs || !capturable || jobs.empty() || n_mom == 0)
     return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
   std::vector<uint64_t> sig = call_signature(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin,
                                              per_mom);
@@ -1004,8 +1069,12 @@ int run_jobs_cached(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t
     int rc = ensure_phase(c, momenta, n_mom, s);   // a call in between may have replaced it
     if (rc) return rc;
     if (!c->graph_exec) return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
+    // the graph's timing events are re-recorded by this replay: read the last one's first
+    if (c->graph_pending) CK(c, harvest_graph_times(c));
     CK(c, cudaGraphLaunch(c->graph_exec, s));
+    c->graph_pending = !c->graph_timed.empty();
     c->last_launches = c->graph_launches;
+    c->last_waves = c->graph_waves;
     c->last_stream = s;
     return BBLOCK_OK;
   }
@@ -1042,6 +1111,7 @@ int run_jobs_cached(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t
   if (rc != BBLOCK_OK || e != cudaSuccess || !graph) {
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
+    drop_graph(c);
     c->last_sig.clear();
     c->err.clear();
     return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
@@ -1051,13 +1121,16 @@ int run_jobs_cached(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    drop_graph(c);
     c->last_sig.clear();
     return run_jobs(c, jobs, momenta, n_mom, spin_idx, coeffs, n_spin, per_mom, s);
   }
   c->graph_exec = exec;
   c->graph_sig = sig;
   c->graph_launches = c->last_launches;
+  c->graph_waves = c->last_waves;
   CK(c, cudaGraphLaunch(exec, s));
+  c->graph_pending = !c->graph_timed.empty();
   c->last_stream = s;
   return BBLOCK_OK;
 }
@@ -1077,7 +1150,7 @@ CallPlan plan_call(const bblock_ctx* c, int n_t, const int nd[3], int n_mom, int
   CallPlan pl;
   const int X = c->X;
   if (fp64_like(c->cfg)) {
-    const int P = std::min(n_mom, kMaxPGroup);
+    const int P = p_group_size(n_mom, c->cfg.precision == BBLOCK_DF64 ? kMaxPGroupDf : kMaxPGroup);
     const Fp64Tile tl = fp64_tile_for(P);
     const int xc = fp64_sites_per_chunk(pairs);
     const int ctas = fp64_contract_ctas_per_sm(P, tl.rn, pairs) * c->num_sms;
@@ -1117,6 +1190,7 @@ int form_code(const bblock_config& cfg) {
   if (cfg.precision == BBLOCK_FP64) return 0;
   if (cfg.precision == BBLOCK_DF64) return 5;
   if (cfg.precision == BBLOCK_TF32X3) return 4;
+  if (cfg.precision == BBLOCK_FP16X3) return 6;
   return cfg.bf16_products == 3 ? 1 : cfg.bf16_products == 9 ? 3 : 2;
 }
 
@@ -1149,7 +1223,7 @@ int bblock_create(bblock_ctx** out, const bblock_config* cfg) {
   const long long X = (long long)cfg->L * cfg->L * cfg->L;
   if (cfg->n_ev < 1 || cfg->n_ev > 3 * X) return BBLOCK_ERR_INVALID_ARG;
   if (cfg->max_ndil < 1 || cfg->max_ndil > 256) return BBLOCK_ERR_INVALID_ARG;
-  if (cfg->precision < BBLOCK_FP64 || cfg->precision > BBLOCK_DF64) return BBLOCK_ERR_INVALID_ARG;
+  if (cfg->precision < BBLOCK_FP64 || cfg->precision > BBLOCK_FP16X3) return BBLOCK_ERR_INVALID_ARG;
   if (cfg->precision == BBLOCK_BF16_SPLIT && cfg->bf16_products != 3 && cfg->bf16_products != 6 &&
       cfg->bf16_products != 9)
     return BBLOCK_ERR_INVALID_ARG;
@@ -1247,7 +1321,7 @@ int bblock_compute(bblock_ctx* c, int n_t, const void* V, const void* phi1, cons
   if (n_t < 0) return fail(c, BBLOCK_ERR_INVALID_ARG, "n_t = %d < 0", n_t);
   int rc = validate_common(c, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom);
   if (rc) return rc;
-  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; return BBLOCK_OK; }
+  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; c->last_waves = 0; return BBLOCK_OK; }
   const size_t vstride = (size_t)c->cfg.n_ev * c->rows;
   const size_t pst[3] = {(size_t)4 * c->cfg.n_ev * nd1, (size_t)4 * c->cfg.n_ev * nd2,
                          (size_t)4 * c->cfg.n_ev * nd3};
@@ -1314,7 +1388,7 @@ int bblock_mode_triplet(bblock_ctx* c, int n_t, const void* V, const int32_t* mo
   const double one[2] = {1.0, 0.0};
   int rc = validate_common(c, momenta, n_mom, spin, one, 1, 0);
   if (rc) return rc;
-  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; return BBLOCK_OK; }
+  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; c->last_waves = 0; return BBLOCK_OK; }
   CK(c, cudaSetDevice(c->cfg.device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!c->d_ident) {
@@ -1357,7 +1431,7 @@ int bblock_from_triplet(bblock_ctx* c, int n_t, const void* T, const void* phi1,
   std::vector<int32_t> mom_dummy(3 * (size_t)std::max(n_mom, 1), 0);
   int rc = validate_common(c, mom_dummy.data(), n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom);
   if (rc) return rc;
-  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; return BBLOCK_OK; }
+  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; c->last_waves = 0; return BBLOCK_OK; }
   const int nds[3] = {nd1, nd2, nd3};
   for (int i = 0; i < 3; ++i)
     if (nds[i] < 1 || nds[i] > c->cfg.max_ndil)
@@ -1448,7 +1522,7 @@ int bblock_compute_host(bblock_ctx* c, int n_t, const void* V, const void* phi1,
   if (n_t < 0) return fail(c, BBLOCK_ERR_INVALID_ARG, "n_t = %d < 0", n_t);
   int rc = validate_common(c, momenta, n_mom, spin_idx, spin_coeffs, n_spin, coeff_per_mom);
   if (rc) return rc;
-  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; return BBLOCK_OK; }
+  if (n_t == 0 || n_mom == 0) { c->last_launches = 0; c->last_waves = 0; return BBLOCK_OK; }
   if (!V || !phi1 || !phi2 || !phi3 || !B_out) return fail(c, BBLOCK_ERR_INVALID_ARG, "a data pointer is NULL");
   const int nds[3] = {nd1, nd2, nd3};
   for (int i = 0; i < 3; ++i)
@@ -1502,7 +1576,7 @@ int bblock_compute_host(bblock_ctx* c, int n_t, const void* V, const void* phi1,
     give_back();
     return cuda_fail(c, e, "enqueueing the input copies");
   }
-  int launches = 0;
+  int launches = 0, waves = 0;
   for (int k = 0; k < n_chunks && rc == BBLOCK_OK && e == cudaSuccess; ++k) {
     const long long t0 = t_of(k), nt = t_of(k + 1) - t0;
     e = cudaStreamWaitEvent(s, ev[1 + k], 0);
@@ -1513,6 +1587,7 @@ int bblock_compute_host(bblock_ctx* c, int n_t, const void* V, const void* phi1,
                         c->d_io + off[4] + t0 * b_t, stream);
     if (rc) break;
     launches += c->last_launches;
+    waves += c->last_waves;
     e = cudaEventRecord(ev[1 + n_chunks + k], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[1 + n_chunks + k], 0);
     if (e == cudaSuccess)
@@ -1531,6 +1606,7 @@ int bblock_compute_host(bblock_ctx* c, int n_t, const void* V, const void* phi1,
   if (e == cudaSuccess) e = e4;
   if (e != cudaSuccess) return cuda_fail(c, e, "pipelined host copies");
   c->last_launches = launches;
+  c->last_waves = waves;
   return BBLOCK_OK;
 }
 
@@ -1540,6 +1616,7 @@ size_t bblock_workspace_bytes(const bblock_ctx* c) {
 }
 
 int bblock_last_launch_count(const bblock_ctx* c) { return c ? c->last_launches : 0; }
+int bblock_last_wave_count(const bblock_ctx* c) { return c ? c->last_waves : 0; }
 
 int bblock_autotune(bblock_ctx* c, int n_t, const void* V, const void* phi1, const void* phi2,
                     const void* phi3, int nd1, int nd2, int nd3, const int32_t* momenta,
@@ -1745,6 +1822,16 @@ int bblock_profile_read(bblock_ctx* c, bblock_kernel_stat* out, int max_entries,
   double ms[K_COUNT] = {};
   int cnt[K_COUNT] = {};
   int rc = BBLOCK_OK;
+  if (c->graph_pending) {
+    cudaError_t e = harvest_graph_times(c);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "bblock_profile_read");
+  }
+  for (int k = 0; k < K_COUNT; ++k) {
+    ms[k] += c->graph_ms[k];
+    cnt[k] += c->graph_cnt[k];
+    c->graph_ms[k] = 0.0;
+    c->graph_cnt[k] = 0;
+  }
   for (auto& t : c->timed) {
     float m = 0.f;
     cudaError_t e = cudaEventSynchronize(t.b);

@@ -8,7 +8,16 @@ namespace bb {
 
 constexpr int kMaxTerms = 4;    // distinct gamma spins folded into one line-3 field
 constexpr int kMaxPairs = 16;   // distinct (alpha, beta) spin pairs
-constexpr int kMaxPGroup = 8;   // momenta handled by one contraction launch
+// Momenta handled by one contraction launch of the FP64 form (10) and of the double-float
+// form (8): the largest counts whose accumulators fit the registers without spills.
+constexpr int kMaxPGroup = 10;
+constexpr int kMaxPGroupDf = 8;
+// Momenta of the first launch: n_mom split into the fewest groups of at most max_group, as
+// evenly as possible (each launch recomputes the colour singlet that its momenta share).
+inline int p_group_size(int n_mom, int max_group) {
+  const int groups = (n_mom + max_group - 1) / max_group;
+  return groups > 0 ? (n_mom + groups - 1) / groups : 0;
+}
 constexpr int kThreads = 256;   // threads per CTA of the FP64 kernels
 
 // Device-side status bits (OR-ed into the context's status word).
@@ -39,6 +48,9 @@ struct ProjFieldF {
   const float2* V;
   const float2* phi;
   float2* q;
+  // if set: the largest |Re| or |Im| written to q is max-ed into *amax (FP32 bits, zeroed
+  // before the projection); the FP16 form scales its operands from it
+  uint32_t* amax;
   int nd;
   int n_terms;
   int row_off[kMaxTerms];
@@ -86,6 +98,9 @@ struct TcJob {
   const float2* q1[4];
   const float2* q2[4];
   const float2* q3[kMaxPairs];
+  // FP16 form: largest |Re| or |Im| of the job's line-1, line-2 and line-3 fields (FP32
+  // bits, written by the projection); null in the other forms
+  const uint32_t* amax;
   float2* partial;               // [n_slab][P][nd1*nd2][nd3]
   double2* B;                    // [P][nd1][nd2][nd3]
   int nd1, nd2, nd3;
@@ -123,7 +138,7 @@ struct TcParams {
   int p_m_tiles, p_n_tiles;
 };
 
-enum TcForm { TC_BF16_3 = 0, TC_BF16_6 = 1, TC_BF16_9 = 2, TC_TF32_3 = 3 };
+enum TcForm { TC_BF16_3 = 0, TC_BF16_6 = 1, TC_BF16_9 = 2, TC_TF32_3 = 3, TC_F16_3 = 4 };
 
 // One input array of a call converted to FP32: n complex128 elements from src to dst.
 struct F32ConvSeg {
@@ -143,6 +158,8 @@ cudaError_t launch_contract_tc(const TcParams& p, int form, int cluster, int gri
 // operand split, accumulated as in the contraction; writes each field's FP32 q.
 cudaError_t launch_project_tc(const TcParams& p, int form, int grid, cudaStream_t s);
 int tc_groups_per_stage(int form);
+// true for the forms that scale their operands from the fields' maxima (TcJob::amax)
+bool tc_form_needs_amax(int form);
 cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab, int P_total,
                                     long long max_elems, int checks, unsigned long long* dbg,
                                     int* status, cudaStream_t s);

@@ -7,6 +7,7 @@
 
 #include "../../include/bblock.h"
 #include "bblock_internal.h"
+#include "fp64_contract.cuh"
 
 namespace bb {
 namespace {
@@ -19,186 +20,53 @@ static __device__ __align__(256) double2 g_noalloc_scratch[kNoallocScratchBytes 
 constexpr int kNaMaxP = 8;
 constexpr int kNaMaxDevices = 64;
 
+// The launch: the shared FP64 contraction body's parameters (one job, embedded below; no
+// status word) plus what this entry point takes instead of a context's tables.
 struct NoallocParams {
-  const double2* q1;      // [4][X][3][nd1]
-  const double2* q2;      // [4][X][3][nd2]
+  ContractParams base;    // jobs = nullptr, status = nullptr, P_total = P, p0 = 0
+  ContractJob job;        // q1/q2 slots = spins 0..3 of the caller's arrays; partial = scratch
   const double2* q3;      // [4][X][3][nd3]
-  double2* partial;       // device address of g_noalloc_scratch: [n_slab][P][nd1*nd2][nd3]
-  int L, X, nd1, nd2, nd3;
-  int m_tiles, n_tiles, n_slab, sites_per_slab;
-  long long total_units;
-  int n_pairs;
-  int pair_alpha[kMaxPairs], pair_beta[kMaxPairs];
+  int L;
   int n_terms[kMaxPairs];
   int term_gamma[kMaxPairs][kMaxTerms];
   double2 term_w[kMaxPairs][kMaxTerms];
   int mom[kNaMaxP][3];
 };
 
-__device__ __forceinline__ double2 na_cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
+// Where the shared body's inputs come from without a context: the single job of the
+// launch, the third quark folded with its pair's spin coefficients while the tile is
+// staged, and the phase evaluated per site from the integer momentum ((n.x) mod L in
+// integers, then sincospi).
+struct NoallocSource {
+  const NoallocParams* np;
+  __device__ const ContractJob& job(long long) const { return np->job; }
+  __device__ double2 third(const ContractJob& J, int pr, int x, int c, int n) const {
+    const int X = np->base.X;
+    double2 b = make_double2(0.0, 0.0);
+    for (int t = 0; t < np->n_terms[pr]; ++t) {
+      const double2 f = np->q3[(((size_t)np->term_gamma[pr][t] * X + x) * 3 + c) * J.nd3 + n];
+      const double2 w = np->term_w[pr][t];
+      b.x = fma(w.x, f.x, fma(-w.y, f.y, b.x));
+      b.y = fma(w.x, f.y, fma(w.y, f.x, b.y));
+    }
+    return b;
+  }
+  __device__ double2 phase(int p, int x) const {
+    const int L = np->L;
+    const long long x0 = x % L, x1 = (x / L) % L, x2 = x / ((long long)L * L);
+    long long kk = np->mom[p][0] * x0 + np->mom[p][1] * x1 + np->mom[p][2] * x2;
+    kk %= L;
+    if (kk < 0) kk += L;
+    double sn, cs;
+    sincospi(2.0 * (double)kk / (double)L, &sn, &cs);
+    return make_double2(cs, -sn);
+  }
+};
 
-// Same arithmetic as k_contract_fp64 for one job; differences: the line fields are read
-// per spin from the caller's [4][X][3][nd] arrays, the spin coefficients are folded into
-// the third-quark tile while it is staged, and the phases are evaluated per site.
 template <int P, int RN>
 __global__ void __launch_bounds__(kThreads, 2)
 k_contract_fp64_noalloc(const __grid_constant__ NoallocParams prm) {
-  constexpr int RM = 2, MT = 16 * RM, NT = 16 * RN;
-  extern __shared__ __align__(16) double smem[];
-  const int np = prm.n_pairs;
-  const int XC = np >= 16 ? 1 : 16 / np;
-  const int KC = XC * np * 3;
-  double* Ar = smem;
-  double* Ai = Ar + KC * MT;
-  double* As = Ai + KC * MT;
-  double* Bc = As + KC * MT;
-  double* Bd = Bc + KC * NT;
-  double* Be = Bd + KC * NT;
-  double2* ph = reinterpret_cast<double2*>(Be + KC * NT);
-  const int tid = threadIdx.x, tn = tid % 16, tm = tid / 16;
-  const int X = prm.X, L = prm.L;
-  const int nd1 = prm.nd1, nd2 = prm.nd2, nd3 = prm.nd3, M = nd1 * nd2;
-
-  for (long long u = blockIdx.x; u < prm.total_units; u += gridDim.x) {
-    long long r = u;
-    const int mt = (int)(r % prm.m_tiles);
-    r /= prm.m_tiles;
-    const int nt = (int)(r % prm.n_tiles);
-    const int slab = (int)(r / prm.n_tiles);
-    const int x_begin = slab * prm.sites_per_slab;
-    const int x_end = min(X, x_begin + prm.sites_per_slab);
-
-    double2 acc[RM][RN][P];
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-      for (int j = 0; j < RN; ++j)
-#pragma unroll
-        for (int p = 0; p < P; ++p) acc[i][j][p] = make_double2(0.0, 0.0);
-
-    for (int xs = x_begin; xs < x_end; xs += XC) {
-      for (int idx = tid; idx < XC * np * MT; idx += kThreads) {
-        const int ml = idx % MT;
-        const int t2 = idx / MT;
-        const int pr = t2 % np, xc = t2 / np;
-        const int x = xs + xc, m = mt * MT + ml;
-        double2 dq0 = make_double2(0.0, 0.0), dq1 = dq0, dq2 = dq0;
-        if (x < x_end && m < M) {
-          const int d1 = m / nd2, d2 = m - d1 * nd2;
-          const double2* u1 = prm.q1 + ((size_t)prm.pair_alpha[pr] * X + x) * 3 * nd1 + d1;
-          const double2* v1 = prm.q2 + ((size_t)prm.pair_beta[pr] * X + x) * 3 * nd2 + d2;
-          const double2 a0 = u1[0], a1 = u1[nd1], a2 = u1[2 * nd1];
-          const double2 b0 = v1[0], b1 = v1[nd2], b2 = v1[2 * nd2];
-          const double2 p12 = na_cmul(a1, b2), p21 = na_cmul(a2, b1);
-          const double2 p20 = na_cmul(a2, b0), p02 = na_cmul(a0, b2);
-          const double2 p01 = na_cmul(a0, b1), p10 = na_cmul(a1, b0);
-          dq0 = make_double2(p12.x - p21.x, p12.y - p21.y);
-          dq1 = make_double2(p20.x - p02.x, p20.y - p02.y);
-          dq2 = make_double2(p01.x - p10.x, p01.y - p10.y);
-        }
-        const int k = (xc * np + pr) * 3;
-        Ar[(k + 0) * MT + ml] = dq0.x; Ai[(k + 0) * MT + ml] = dq0.y; As[(k + 0) * MT + ml] = dq0.x + dq0.y;
-        Ar[(k + 1) * MT + ml] = dq1.x; Ai[(k + 1) * MT + ml] = dq1.y; As[(k + 1) * MT + ml] = dq1.x + dq1.y;
-        Ar[(k + 2) * MT + ml] = dq2.x; Ai[(k + 2) * MT + ml] = dq2.y; As[(k + 2) * MT + ml] = dq2.x + dq2.y;
-      }
-      for (int idx = tid; idx < KC * NT; idx += kThreads) {
-        const int nl = idx % NT;
-        const int k = idx / NT;
-        const int c = k % 3, t2 = k / 3;
-        const int pr = t2 % np, xc = t2 / np;
-        const int x = xs + xc, n = nt * NT + nl;
-        double2 b = make_double2(0.0, 0.0);
-        if (x < x_end && n < nd3) {
-          for (int t = 0; t < prm.n_terms[pr]; ++t) {
-            const double2 f = prm.q3[(((size_t)prm.term_gamma[pr][t] * X + x) * 3 + c) * nd3 + n];
-            const double2 w = prm.term_w[pr][t];
-            b.x = fma(w.x, f.x, fma(-w.y, f.y, b.x));
-            b.y = fma(w.x, f.y, fma(w.y, f.x, b.y));
-          }
-        }
-        Bc[k * NT + nl] = b.x;
-        Bd[k * NT + nl] = b.y - b.x;
-        Be[k * NT + nl] = b.x + b.y;
-      }
-      for (int idx = tid; idx < XC * P; idx += kThreads) {
-        const int p = idx % P, xc = idx / P;
-        const int x = xs + xc;
-        double2 e = make_double2(0.0, 0.0);
-        if (x < x_end) {
-          const long long x0 = x % L, x1 = (x / L) % L, x2 = x / ((long long)L * L);
-          long long kk = prm.mom[p][0] * x0 + prm.mom[p][1] * x1 + prm.mom[p][2] * x2;
-          kk %= L;
-          if (kk < 0) kk += L;
-          double sn, cs;
-          sincospi(2.0 * (double)kk / (double)L, &sn, &cs);
-          e = make_double2(cs, -sn);
-        }
-        ph[idx] = e;
-      }
-      __syncthreads();
-
-      for (int xc = 0; xc < XC; ++xc) {
-        double k1[RM][RN], k2[RM][RN], k3[RM][RN];
-#pragma unroll
-        for (int i = 0; i < RM; ++i)
-#pragma unroll
-          for (int j = 0; j < RN; ++j) k1[i][j] = k2[i][j] = k3[i][j] = 0.0;
-        const int kbeg = xc * np * 3, kend = kbeg + np * 3;
-        for (int k = kbeg; k < kend; ++k) {
-          double ar[RM], ai[RM], as[RM], bc[RN], bd[RN], be[RN];
-#pragma unroll
-          for (int i = 0; i < RM; ++i) {
-            ar[i] = Ar[k * MT + tm + 16 * i];
-            ai[i] = Ai[k * MT + tm + 16 * i];
-            as[i] = As[k * MT + tm + 16 * i];
-          }
-#pragma unroll
-          for (int j = 0; j < RN; ++j) {
-            bc[j] = Bc[k * NT + tn + 16 * j];
-            bd[j] = Bd[k * NT + tn + 16 * j];
-            be[j] = Be[k * NT + tn + 16 * j];
-          }
-#pragma unroll
-          for (int i = 0; i < RM; ++i)
-#pragma unroll
-            for (int j = 0; j < RN; ++j) {
-              k1[i][j] = fma(bc[j], as[i], k1[i][j]);
-              k2[i][j] = fma(ar[i], bd[j], k2[i][j]);
-              k3[i][j] = fma(ai[i], be[j], k3[i][j]);
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          const double2 e = ph[xc * P + p];
-#pragma unroll
-          for (int i = 0; i < RM; ++i)
-#pragma unroll
-            for (int j = 0; j < RN; ++j) {
-              const double sr = k1[i][j] - k3[i][j], si = k1[i][j] + k2[i][j];
-              acc[i][j][p].x = fma(e.x, sr, fma(-e.y, si, acc[i][j][p].x));
-              acc[i][j][p].y = fma(e.x, si, fma(e.y, sr, acc[i][j][p].y));
-            }
-        }
-      }
-      __syncthreads();
-    }
-
-#pragma unroll
-    for (int i = 0; i < RM; ++i) {
-      const int m = mt * MT + tm + 16 * i;
-      if (m >= M) continue;
-#pragma unroll
-      for (int j = 0; j < RN; ++j) {
-        const int n = nt * NT + tn + 16 * j;
-        if (n >= nd3) continue;
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-          prm.partial[(((size_t)slab * P + p) * M + m) * nd3 + n] = acc[i][j][p];
-      }
-    }
-  }
+  fp64c::contract_body<P, 2, RN>(prm.base, NoallocSource{&prm});
 }
 
 // B[e] = sum over slabs of partial[slab][e], slabs in index order.
@@ -216,15 +84,10 @@ __global__ void k_reduce_noalloc(const double2* __restrict__ partial, double2* _
   }
 }
 
-size_t na_smem_bytes(int P, int rn, int n_pairs) {
-  const int xc = fp64_sites_per_chunk(n_pairs);
-  const int kc = xc * n_pairs * 3;
-  return sizeof(double) * 3 * (size_t)kc * (32 + 16 * rn) + sizeof(double2) * xc * P;
-}
 
 template <int P, int RN>
 cudaError_t na_launch(const NoallocParams& prm, int grid, cudaStream_t s) {
-  const size_t smem = na_smem_bytes(P, RN, prm.n_pairs);
+  const size_t smem = fp64_contract_smem_bytes(P, RN, prm.base.n_pairs);
   cudaError_t e = cudaFuncSetAttribute(k_contract_fp64_noalloc<P, RN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -256,6 +119,28 @@ cudaError_t na_dispatch(const NoallocParams& prm, int P, int rn, int grid, cudaS
 // cudaGetSymbolAddress once per device while that device is current.
 std::mutex g_na_mu;
 void* g_na_addr[kNaMaxDevices] = {};
+void* g_na_ctx[kNaMaxDevices] = {};   // the CUDA context each address was looked up in
+
+// The calling thread's current CUDA context (driver API, reached through the runtime's
+// entry-point query so that the library needs no link against libcuda), or nullptr.
+void* na_current_context() {
+  typedef int (*CtxGetCurrentFn)(void**);
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(f);
+    else
+      cudaGetLastError();
+  }
+  void* ctx = nullptr;
+  if (fn && fn(&ctx) != 0) ctx = nullptr;
+  return ctx;
+}
 
 int na_fail(char* err, size_t err_len, int code, const char* msg) {
   if (err && err_len) snprintf(err, err_len, "%s", msg);
@@ -308,12 +193,22 @@ extern "C" int bblock_contract_noalloc(int L, const void* q1, const void* q2, co
                      "q1, q2, q3 and B_out must be device memory of the current device");
 
   NoallocParams prm{};
-  prm.q1 = static_cast<const double2*>(q1);
-  prm.q2 = static_cast<const double2*>(q2);
+  ContractParams& base = prm.base;
+  ContractJob& job = prm.job;
+  const int X = L * L * L;
+  // the q1 / q2 slots are the four spins of the caller's arrays; a pair names its spins
+  for (int a = 0; a < 4; ++a) {
+    job.q1[a] = static_cast<const double2*>(q1) + (size_t)a * X * 3 * nd1;
+    job.q2[a] = static_cast<const double2*>(q2) + (size_t)a * X * 3 * nd2;
+  }
+  job.nd1 = nd1; job.nd2 = nd2; job.nd3 = nd3;
+  job.unit_begin = 0;
   prm.q3 = static_cast<const double2*>(q3);
   prm.L = L;
-  prm.X = L * L * L;
-  prm.nd1 = nd1; prm.nd2 = nd2; prm.nd3 = nd3;
+  base.X = X;
+  base.n_jobs = 1;
+  base.P_total = n_mom;
+  base.p0 = 0;
   for (int p = 0; p < n_mom; ++p)
     for (int i = 0; i < 3; ++i) prm.mom[p][i] = momenta[3 * p + i];
   // spin triples -> (alpha, beta) pairs with the coefficient-weighted gamma terms
@@ -322,12 +217,12 @@ extern "C" int bblock_contract_noalloc(int L, const void* q1, const void* q2, co
     if (al < 0 || al > 3 || be < 0 || be > 3 || ga < 0 || ga > 3)
       return na_fail(err, err_len, BBLOCK_ERR_INVALID_ARG, "spin index outside 0..3");
     int pr = -1;
-    for (int k = 0; k < prm.n_pairs; ++k)
-      if (prm.pair_alpha[k] == al && prm.pair_beta[k] == be) pr = k;
+    for (int k = 0; k < base.n_pairs; ++k)
+      if (base.a_slot[k] == al && base.b_slot[k] == be) pr = k;
     if (pr < 0) {
-      pr = prm.n_pairs++;
-      prm.pair_alpha[pr] = al;
-      prm.pair_beta[pr] = be;
+      pr = base.n_pairs++;
+      base.a_slot[pr] = al;
+      base.b_slot[pr] = be;
     }
     int t = -1;
     for (int k = 0; k < prm.n_terms[pr]; ++k)
@@ -342,18 +237,20 @@ extern "C" int bblock_contract_noalloc(int L, const void* q1, const void* q2, co
   }
 
   const Fp64Tile tl = fp64_tile_for(n_mom);
-  prm.m_tiles = (nd1 * nd2 + 31) / 32;
-  prm.n_tiles = (nd3 + 16 * tl.rn - 1) / (16 * tl.rn);
+  job.m_tiles = (nd1 * nd2 + 16 * tl.rm - 1) / (16 * tl.rm);
+  job.n_tiles = (nd3 + 16 * tl.rn - 1) / (16 * tl.rn);
   const size_t per = (size_t)n_mom * nd1 * nd2 * nd3;
   const size_t max_slabs_fit = kNoallocScratchBytes / (per * sizeof(double2));
   if (max_slabs_fit < 1)
     return na_fail(err, err_len, BBLOCK_ERR_TOO_LARGE,
                    "n_mom*nd1*nd2*nd3*16 bytes exceeds the static scratch of this entry point");
 
-  // one-time set-up on this device: device address of the static scratch
+  // set-up once per device and CUDA context: the device address of the static scratch
+  // (looked up again if the device's context was reset and recreated since)
   {
     std::lock_guard<std::mutex> lock(g_na_mu);
-    if (!g_na_addr[dev]) {
+    void* ctx = na_current_context();
+    if (!g_na_addr[dev] || ctx != g_na_ctx[dev]) {
       void* addr = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
       if (e != cudaSuccess || !addr) {
@@ -361,8 +258,9 @@ extern "C" int bblock_contract_noalloc(int L, const void* q1, const void* q2, co
         return na_fail(err, err_len, BBLOCK_ERR_CUDA, "cudaGetSymbolAddress of the scratch failed");
       }
       g_na_addr[dev] = addr;
+      g_na_ctx[dev] = ctx;
     }
-    prm.partial = static_cast<double2*>(g_na_addr[dev]);
+    job.partial = static_cast<double2*>(g_na_addr[dev]);
   }
 
   int num_sms = 0;
@@ -370,28 +268,28 @@ extern "C" int bblock_contract_noalloc(int L, const void* q1, const void* q2, co
     cudaGetLastError();
     return na_fail(err, err_len, BBLOCK_ERR_CUDA, "device query failed");
   }
-  const int xc = fp64_sites_per_chunk(prm.n_pairs);
+  const int xc = fp64_sites_per_chunk(base.n_pairs);
   const int grid_cap = 2 * num_sms;
-  const long long tiles = (long long)prm.m_tiles * prm.n_tiles;
+  const long long tiles = (long long)job.m_tiles * job.n_tiles;
   long long want = (4LL * grid_cap + tiles - 1) / tiles;
   long long n_slab = want;
   if (n_slab > (long long)max_slabs_fit) n_slab = (long long)max_slabs_fit;
-  if (n_slab > (prm.X + xc - 1) / xc) n_slab = (prm.X + xc - 1) / xc;
+  if (n_slab > (X + xc - 1) / xc) n_slab = (X + xc - 1) / xc;
   if (n_slab < 1) n_slab = 1;
-  int sps = (int)((prm.X + n_slab - 1) / n_slab);
+  int sps = (int)((X + n_slab - 1) / n_slab);
   sps = (sps + xc - 1) / xc * xc;
-  prm.sites_per_slab = sps;
-  prm.n_slab = (prm.X + sps - 1) / sps;
-  prm.total_units = tiles * prm.n_slab;
-  const int grid = (int)(prm.total_units < grid_cap ? prm.total_units : grid_cap);
+  base.sites_per_slab = sps;
+  base.n_slab = (X + sps - 1) / sps;
+  base.total_units = tiles * base.n_slab;
+  const int grid = (int)(base.total_units < grid_cap ? base.total_units : grid_cap);
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = na_dispatch(prm, n_mom, tl.rn, grid, s);
   if (e == cudaSuccess) {
     long long bx = ((long long)per + kThreads - 1) / kThreads;
     if (bx > 4096) bx = 4096;
-    k_reduce_noalloc<<<(unsigned)bx, kThreads, 0, s>>>(prm.partial, static_cast<double2*>(B_out),
-                                                       (long long)per, prm.n_slab);
+    k_reduce_noalloc<<<(unsigned)bx, kThreads, 0, s>>>(job.partial, static_cast<double2*>(B_out),
+                                                       (long long)per, base.n_slab);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

@@ -9,7 +9,8 @@
 //                   outputs per thread, the next K block's loads in flight while the
 //                   current one is multiplied); the grid runs the fields of a row tile back
 //                   to back (blockIdx.x = field) so that the V tile they share is served
-//                   from L2.
+//                   from L2. Optionally it also records the largest |Re| or |Im| of each
+//                   field it writes (the FP16 form's operand scales).
 #include "bblock_internal.h"
 
 namespace bb {
@@ -121,6 +122,9 @@ __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __re
     }
     __syncthreads();
   }
+  // largest |Re| or |Im| written by this thread, as FP32 bits (the integer order of
+  // non-negative floats; NaN above infinity above every finite value)
+  uint32_t amax = 0u;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int row = m0 + 4 * tm + i;
@@ -129,9 +133,16 @@ __global__ void __launch_bounds__(kThreads) k_project_f32(const ProjFieldF* __re
     for (int j = 0; j < 4; ++j) {
       const int col = n0 + 4 * tn + j;
       if (col < nd && (!checks || f32_idx_ok((long long)row * nd + col, (long long)rows * nd, 13,
-                                              blockIdx.x, dbg, status)))
+                                              blockIdx.x, dbg, status))) {
         F.q[(size_t)row * nd + col] = acc[i][j];
+        amax = max(amax, max(__float_as_uint(fabsf(acc[i][j].x)),
+                             __float_as_uint(fabsf(acc[i][j].y))));
+      }
     }
+  }
+  if (F.amax) {   // uniform over the CTA
+    amax = __reduce_max_sync(0xffffffffu, amax);
+    if ((threadIdx.x & 31) == 0 && amax) atomicMax(F.amax, amax);
   }
 }
 __global__ void k_convert_f32(const F32ConvSeg* __restrict__ segs) {

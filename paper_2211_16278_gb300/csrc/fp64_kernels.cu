@@ -18,15 +18,9 @@
 //     9*n_pairs + 2 + 4*P FP64 operations instead of n_pairs*(12 + 4P);
 //   * the diquark of a (d1,d2) tile is built once per site and reused for every d3.
 #include "bblock_internal.h"
+#include "fp64_contract.cuh"
 
 namespace bb {
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 csub(double2 a, double2 b) {
-  return make_double2(a.x - b.x, a.y - b.y);
-}
 
 // ------------------------------------------------------------------ phases
 
@@ -161,13 +155,9 @@ cudaError_t launch_project_fp64(const ProjField* d_fields, int n_fields, int row
 
 // ------------------------------------------------------------------ contraction (Eq. 1/3)
 //
-// Work unit = (job, slab of sites, 16*RM (d1,d2) pairs, 16*RN d3 columns). Per chunk of XC
-// sites the CTA stages in shared memory
-//   A[k][m] = diquark  (q1_alpha x q2_beta)_c (x) for pair index m = d1*nd2 + d2,
-//   B[k][n] = q3f_pair[x][c][d3 = n],
-// with k = (site, pair, colour). Each thread then owns RM x RN (m, n) outputs and per site
-//   singlet = sum_{pair, c} A[k][m] * B[k][n]          (three-multiplication form)
-//   acc[p] += e^{-i p.x} * singlet                      for the P momenta of the launch.
+// The body is fp64c::contract_body (fp64_contract.cuh); here the work units come from the
+// context's job table, the third quark from the coefficient-folded line-3 fields and the
+// phases from the cached table.
 
 size_t fp64_contract_smem_bytes(int P, int rn, int n_pairs) {
   const int xc = fp64_sites_per_chunk(n_pairs);
@@ -175,161 +165,22 @@ size_t fp64_contract_smem_bytes(int P, int rn, int n_pairs) {
   return sizeof(double) * 3 * (size_t)kc * (16 * 2 + 16 * rn) + sizeof(double2) * xc * P;
 }
 
-__device__ __forceinline__ int find_job(const ContractJob* jobs, int n_jobs, long long u) {
-  int lo = 0, hi = n_jobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+struct TableSource {
+  const ContractParams* prm;
+  __device__ const ContractJob& job(long long u) const {
+    return prm->jobs[fp64c::find_job(prm->jobs, prm->n_jobs, u)];
   }
-  return lo;
-}
+  __device__ double2 third(const ContractJob& J, int pr, int x, int c, int n) const {
+    return J.q3[pr][((size_t)x * 3 + c) * J.nd3 + n];
+  }
+  __device__ double2 phase(int p, int x) const {
+    return prm->phase[(size_t)(prm->p0 + p) * prm->X + x];
+  }
+};
 
 template <int P, int RM, int RN>
 __global__ void __launch_bounds__(kThreads, 2) k_contract_fp64(const __grid_constant__ ContractParams prm) {
-  constexpr int MT = 16 * RM, NT = 16 * RN;
-  extern __shared__ __align__(16) double smem[];
-  const int np = prm.n_pairs;
-  const int XC = np >= 16 ? 1 : 16 / np;
-  const int KC = XC * np * 3;
-  double* __restrict__ Ar = smem;
-  double* __restrict__ Ai = Ar + KC * MT;
-  double* __restrict__ As = Ai + KC * MT;
-  double* __restrict__ Bc = As + KC * MT;
-  double* __restrict__ Bd = Bc + KC * NT;
-  double* __restrict__ Be = Bd + KC * NT;
-  double2* __restrict__ ph = reinterpret_cast<double2*>(Be + KC * NT);
-
-  const int tid = threadIdx.x, tn = tid % 16, tm = tid / 16;
-  const int X = prm.X;
-
-  for (long long u = blockIdx.x; u < prm.total_units; u += gridDim.x) {
-    const ContractJob& J = prm.jobs[find_job(prm.jobs, prm.n_jobs, u)];
-    const int nd1 = J.nd1, nd2 = J.nd2, nd3 = J.nd3;
-    const int M = nd1 * nd2;
-    long long r = u - J.unit_begin;
-    const int mt = (int)(r % J.m_tiles);
-    r /= J.m_tiles;
-    const int nt = (int)(r % J.n_tiles);
-    const int slab = (int)(r / J.n_tiles);
-    if (slab >= prm.n_slab) {  // inconsistent job table: flag it, skip the unit
-      if (tid == 0) atomicOr(prm.status, kStatusBadJob);
-      continue;
-    }
-    const int x_begin = slab * prm.sites_per_slab;
-    const int x_end = min(X, x_begin + prm.sites_per_slab);
-
-    double2 acc[RM][RN][P];
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-      for (int j = 0; j < RN; ++j)
-#pragma unroll
-        for (int p = 0; p < P; ++p) acc[i][j][p] = make_double2(0.0, 0.0);
-
-    for (int xs = x_begin; xs < x_end; xs += XC) {
-      // --- diquark tile: A[(xc, pair, c)][m]
-      for (int idx = tid; idx < XC * np * MT; idx += kThreads) {
-        const int ml = idx % MT;
-        const int t2 = idx / MT;
-        const int pr = t2 % np, xc = t2 / np;
-        const int x = xs + xc, m = mt * MT + ml;
-        double2 dq0 = make_double2(0.0, 0.0), dq1 = dq0, dq2 = dq0;
-        if (x < x_end && m < M) {
-          const int d1 = m / nd2, d2 = m - d1 * nd2;
-          const double2* u = J.q1[prm.a_slot[pr]] + (size_t)x * 3 * nd1 + d1;
-          const double2* v = J.q2[prm.b_slot[pr]] + (size_t)x * 3 * nd2 + d2;
-          const double2 u0 = u[0], u1 = u[nd1], u2 = u[2 * nd1];
-          const double2 v0 = v[0], v1 = v[nd2], v2 = v[2 * nd2];
-          dq0 = csub(cmul(u1, v2), cmul(u2, v1));   // eps_{120}, eps_{210}
-          dq1 = csub(cmul(u2, v0), cmul(u0, v2));   // eps_{201}, eps_{021}
-          dq2 = csub(cmul(u0, v1), cmul(u1, v0));   // eps_{012}, eps_{102}
-        }
-        const int k = (xc * np + pr) * 3;
-        Ar[(k + 0) * MT + ml] = dq0.x; Ai[(k + 0) * MT + ml] = dq0.y; As[(k + 0) * MT + ml] = dq0.x + dq0.y;
-        Ar[(k + 1) * MT + ml] = dq1.x; Ai[(k + 1) * MT + ml] = dq1.y; As[(k + 1) * MT + ml] = dq1.x + dq1.y;
-        Ar[(k + 2) * MT + ml] = dq2.x; Ai[(k + 2) * MT + ml] = dq2.y; As[(k + 2) * MT + ml] = dq2.x + dq2.y;
-      }
-      // --- third quark tile: B[(xc, pair, c)][n]
-      for (int idx = tid; idx < KC * NT; idx += kThreads) {
-        const int nl = idx % NT;
-        const int k = idx / NT;
-        const int c = k % 3, t2 = k / 3;
-        const int pr = t2 % np, xc = t2 / np;
-        const int x = xs + xc, n = nt * NT + nl;
-        double2 b = make_double2(0.0, 0.0);
-        if (x < x_end && n < nd3) b = J.q3[pr][((size_t)x * 3 + c) * nd3 + n];
-        Bc[k * NT + nl] = b.x;
-        Bd[k * NT + nl] = b.y - b.x;
-        Be[k * NT + nl] = b.x + b.y;
-      }
-      // --- phases of the chunk's sites
-      for (int idx = tid; idx < XC * P; idx += kThreads) {
-        const int p = idx % P, xc = idx / P;
-        const int x = xs + xc;
-        ph[idx] = x < x_end ? prm.phase[(size_t)(prm.p0 + p) * X + x] : make_double2(0.0, 0.0);
-      }
-      __syncthreads();
-
-      for (int xc = 0; xc < XC; ++xc) {
-        double k1[RM][RN], k2[RM][RN], k3[RM][RN];
-#pragma unroll
-        for (int i = 0; i < RM; ++i)
-#pragma unroll
-          for (int j = 0; j < RN; ++j) k1[i][j] = k2[i][j] = k3[i][j] = 0.0;
-        const int kbeg = xc * np * 3, kend = kbeg + np * 3;
-        for (int k = kbeg; k < kend; ++k) {
-          double ar[RM], ai[RM], as[RM], bc[RN], bd[RN], be[RN];
-#pragma unroll
-          for (int i = 0; i < RM; ++i) {
-            ar[i] = Ar[k * MT + tm + 16 * i];
-            ai[i] = Ai[k * MT + tm + 16 * i];
-            as[i] = As[k * MT + tm + 16 * i];
-          }
-#pragma unroll
-          for (int j = 0; j < RN; ++j) {
-            bc[j] = Bc[k * NT + tn + 16 * j];
-            bd[j] = Bd[k * NT + tn + 16 * j];
-            be[j] = Be[k * NT + tn + 16 * j];
-          }
-#pragma unroll
-          for (int i = 0; i < RM; ++i)
-#pragma unroll
-            for (int j = 0; j < RN; ++j) {
-              k1[i][j] = fma(bc[j], as[i], k1[i][j]);
-              k2[i][j] = fma(ar[i], bd[j], k2[i][j]);
-              k3[i][j] = fma(ai[i], be[j], k3[i][j]);
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          const double2 e = ph[xc * P + p];
-#pragma unroll
-          for (int i = 0; i < RM; ++i)
-#pragma unroll
-            for (int j = 0; j < RN; ++j) {
-              const double sr = k1[i][j] - k3[i][j], si = k1[i][j] + k2[i][j];
-              acc[i][j][p].x = fma(e.x, sr, fma(-e.y, si, acc[i][j][p].x));
-              acc[i][j][p].y = fma(e.x, si, fma(e.y, sr, acc[i][j][p].y));
-            }
-        }
-      }
-      __syncthreads();
-    }
-
-#pragma unroll
-    for (int i = 0; i < RM; ++i) {
-      const int m = mt * MT + tm + 16 * i;
-      if (m >= M) continue;
-#pragma unroll
-      for (int j = 0; j < RN; ++j) {
-        const int n = nt * NT + tn + 16 * j;
-        if (n >= nd3) continue;
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-          J.partial[(((size_t)slab * prm.P_total + prm.p0 + p) * M + m) * nd3 + n] = acc[i][j][p];
-      }
-    }
-  }
+  fp64c::contract_body<P, RM, RN>(prm, TableSource{&prm});
 }
 
 template <int P, int RN>
@@ -342,7 +193,8 @@ static cudaError_t launch_contract_p(const ContractParams& prm, int grid, cudaSt
   return cudaGetLastError();
 }
 
-// (P, RN) instantiations: RN = 2 only for P <= 4 (register budget of 128 per thread).
+// (P, RN) instantiations: RN = 2 only for P <= 4 (register budget of 128 per thread);
+// RN = 1 up to P = 10, the largest momentum group that runs without spills.
 cudaError_t launch_contract_fp64(const ContractParams& prm, int P, int rn, int grid,
                                  cudaStream_t s) {
   if (prm.total_units == 0) return cudaSuccess;
@@ -364,6 +216,8 @@ cudaError_t launch_contract_fp64(const ContractParams& prm, int P, int rn, int g
     case 6: return launch_contract_p<6, 1>(prm, grid, s);
     case 7: return launch_contract_p<7, 1>(prm, grid, s);
     case 8: return launch_contract_p<8, 1>(prm, grid, s);
+    case 9: return launch_contract_p<9, 1>(prm, grid, s);
+    case 10: return launch_contract_p<10, 1>(prm, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -41,6 +41,7 @@
 // their loops without waiting or computing, the MMA thread waits (bounded) for its
 // outstanding MMAs and the allocating warp frees TMEM.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 #include "bblock_internal.h"
@@ -88,8 +89,8 @@ constexpr int kBPlaneBytes = kMaxNC * 96;        // room for one plane of up to 
 // The 2-piece BF16 form, bound by its producers, loses 2-4 % to the extra -Bi stores and
 // the larger stages (less L1 for the producers' loads): it keeps two planes, Br | Bi, and
 // four MMAs of N = NC.
-template <bool TF32, int LEVELS> struct TcLayout {
-  static constexpr bool kTwoMma = TF32 || LEVELS == 3;
+template <bool TF32, int LEVELS, bool F16 = false> struct TcLayout {
+  static constexpr bool kTwoMma = TF32 || LEVELS == 3 || F16;
   static constexpr int kBPlanes = kTwoMma ? 3 : 2;
   static constexpr int kBr = kTwoMma ? 1 : 0, kBi = kBr + 1;   // plane slots; -Bi is slot 0
   static constexpr int kStages = LEVELS == 3 ? 2 : 3;
@@ -305,6 +306,32 @@ __device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const
   }
 }
 
+// FP16 hi/lo pieces of 8 FP32 values already scaled into FP16's range (|v| < 2^15):
+//   hi = rn16(v), lo = rn16(v - hi);
+// v - hi is exact in FP32, so v = hi + lo + r with |r| <= 2^-23 |v| while lo is a normal
+// FP16 number (smaller values keep an absolute error below 2^-25). Round-to-nearest-even is
+// symmetric under negation, so the pieces of -v are the stored pieces with the sign bits
+// (bit 15 of each half) flipped.
+__device__ __forceinline__ void split_store8_f16(const float (&v)[8], uint8_t* const (&dst)[2],
+                                                 uint8_t* const* neg) {
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);   // .x = low 16 bits
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    hw[i] = *reinterpret_cast<const uint32_t*>(&h);
+    lw[i] = *reinterpret_cast<const uint32_t*>(&l);
+  }
+  *reinterpret_cast<uint4*>(dst[0]) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *reinterpret_cast<uint4*>(dst[1]) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  if (neg) {
+    constexpr uint32_t m = 0x80008000u;
+    *reinterpret_cast<uint4*>(neg[0]) = make_uint4(hw[0] ^ m, hw[1] ^ m, hw[2] ^ m, hw[3] ^ m);
+    *reinterpret_cast<uint4*>(neg[1]) = make_uint4(lw[0] ^ m, lw[1] ^ m, lw[2] ^ m, lw[3] ^ m);
+  }
+}
+
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -321,6 +348,31 @@ __device__ __forceinline__ int tc_find_job(const TcJob* jobs, int n_jobs, long l
 struct Unit {
   int job, mt, nt, slab, x_begin, x_end, n_stages;
 };
+
+// Power-of-two scales of the FP16 form, from the largest |Re| or |Im| (FP32 bits) of the
+// fields of each quark line of a job, amax[0..2]. With e_i = floor(log2 max_i):
+//   diquark  |Re|, |Im| of q1_a q2_b - q1_b q2_a  <= 4 max_1 max_2 < 2^(e1 + e2 + 4),
+//   phase x third quark                             <= sqrt(2) max_3  < 2^(e3 + 1.5),
+// so the scales 2^eA with eA = 10 - e1 - e2 and 2^eB with eB = 12 - e3 keep both operands
+// below 2^14 (FP16 holds up to 65504). Both are clamped to normal FP32 powers of two; the
+// clamp only binds where FP32 itself would overflow or the values are below 2^-116. The
+// slab reduction divides the sum by 2^(eA + eB) in FP64 (exact). A zero or non-finite
+// maximum gives a clamped exponent; non-finite inputs stay non-finite.
+__device__ __forceinline__ int f16_floor_log2(uint32_t bits) {
+  const int be = (int)((bits >> 23) & 0xFFu);
+  if (be == 0xFF) return 200;                           // inf or NaN
+  if ((bits & 0x7FFFFFFFu) == 0u) return -200;          // zero
+  return be == 0 ? -127 : be - 127;                     // subnormal: max < 2^-126
+}
+__device__ __forceinline__ void f16_scale_exps(const uint32_t* amax, int& eA, int& eB) {
+  const int e1 = f16_floor_log2(amax[0]), e2 = f16_floor_log2(amax[1]);
+  const int e3 = f16_floor_log2(amax[2]);
+  eA = min(126, max(-126, 10 - e1 - e2));
+  eB = min(126, max(-126, 12 - e3));
+}
+__device__ __forceinline__ float pow2f(int e) {        // e in [-126, 127]
+  return __int_as_float((127 + e) << 23);
+}
 
 // Index check of the debug option: false (and the first violation recorded) if i is
 // outside [0, n).
@@ -393,14 +445,16 @@ __device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t parity,
 // with m = (site, colour) and Phi the coefficient-folded phi columns of one field; the same
 // pipeline with the K index of a stage read as the eigenvector index
 // l = stage * 3G + colour * G + group, and the unit's sum written as the FP32 field.
-template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C, bool PROJ>
+template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C, bool PROJ, bool F16 = false>
 __device__ __forceinline__ void tc_body(const TcParams& prm) {
   using R = Roles<TF32, C>;
   static_assert(!PROJ || (C == 1 && !CHECKS), "the projection runs without clusters or checks");
+  static_assert(!F16 || (!TF32 && LEVELS == 2 && C == 1 && !PROJ),
+                "the FP16 form: two pieces, no cluster, contraction only");
   constexpr int G = TF32 ? 8 : 16;                 // (site, pair) groups per stage
   // transaction bytes a stage receives from the peers: their diquark rows, every plane
   constexpr uint32_t kPeerTx = (uint32_t)((C - 1) * (R::kARows / 8) * 768 * LEVELS * 2);
-  using Lay = TcLayout<TF32, LEVELS>;
+  using Lay = TcLayout<TF32, LEVELS, F16>;
   constexpr int STAGES = Lay::kStages;
   constexpr int STAGE_BYTES = Lay::kStageBytes;
   constexpr bool kTwoMma = Lay::kTwoMma;   // complex product as two N = 2 NC MMAs
@@ -501,6 +555,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
       bool row_ok = false;
       int off1 = 0, off2 = 0, s1 = 0, s2 = 0, pidx = 0;
       const float2* phase_p = nullptr;
+      float f16s = 1.f;   // FP16 form: this row's power-of-two scale (diquark or phase side)
       // projection: the unit's field, read once per unit (A: V column m; B: the folded
       // phi column n, its terms' rows and FP32 weights)
       const float2* p_src = nullptr;
@@ -527,6 +582,11 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
       } else {
         const TcJob& J = prm.jobs[w.job];
         const int nd1 = J.nd1, nd2 = J.nd2, nd3 = J.nd3;
+        if constexpr (F16) {
+          int eA, eB;
+          f16_scale_exps(J.amax, eA, eB);
+          f16s = pow2f(is_a ? eA : eB);
+        }
         if (is_a) {
           // M side: diquark of the pair m = d1 * nd2 + d2
           const int m = w.mt * kTcM + rr;
@@ -652,10 +712,17 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                   c0 = make_float2(a12.x - a21.x, a12.y - a21.y);
                   c1 = make_float2(a20.x - a02.x, a20.y - a02.y);
                   c2 = make_float2(a01.x - a10.x, a01.y - a10.y);
+                  if constexpr (F16) {
+                    c0.x *= f16s; c0.y *= f16s;
+                    c1.x *= f16s; c1.y *= f16s;
+                    c2.x *= f16s; c2.y *= f16s;
+                  }
                 } else {
-                  c0 = cmulf(ld[j][3], ld[j][0]);
-                  c1 = cmulf(ld[j][3], ld[j][1]);
-                  c2 = cmulf(ld[j][3], ld[j][2]);
+                  float2 ph = ld[j][3];
+                  if constexpr (F16) { ph.x *= f16s; ph.y *= f16s; }
+                  c0 = cmulf(ph, ld[j][0]);
+                  c1 = cmulf(ph, ld[j][1]);
+                  c2 = cmulf(ph, ld[j][2]);
                 }
                 const int jj = half * kLoadRun + j;
                 vmask |= (uint32_t)vld[j] << jj;
@@ -694,7 +761,10 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
               dn[l] = smem + b_plane(slot, l, 0) + o;
             }
             uint8_t* const* neg = (is_a || !kTwoMma) ? nullptr : dn;
-            if constexpr (TF32) {
+            if constexpr (F16) {
+              split_store8_f16(re[c], dr, nullptr);
+              split_store8_f16(im[c], di, neg);
+            } else if constexpr (TF32) {
               split_store8<TF32, LEVELS>(re[c], dr, nullptr);
               split_store8<TF32, LEVELS>(im[c], di, neg);
             } else {
@@ -740,7 +810,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issue (one thread)
     if (lane == 0) {
-      const uint32_t fmt = TF32 ? 2u : 1u;
+      const uint32_t fmt = TF32 ? 2u : (F16 ? 0u : 1u);   // TF32, FP16 or BF16 operands
       // FP32 accumulate, A and B of the same type, K-major, M = 128, N = 2 NC or NC
       const uint32_t n_mma = kTwoMma ? 2 * NC : NC;
       const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) |
@@ -916,10 +986,10 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   }
 }
 
-template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C>
+template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C, bool F16>
 __global__ void __launch_bounds__(Roles<TF32, C>::kThreads, 1)
 k_contract_tc(const __grid_constant__ TcParams prm) {
-  tc_body<TF32, LEVELS, NPROD, CHECKS, C, false>(prm);
+  tc_body<TF32, LEVELS, NPROD, CHECKS, C, false, F16>(prm);
 }
 template <bool TF32, int LEVELS, int NPROD>
 __global__ void __launch_bounds__(Roles<TF32, 1>::kThreads, 1)
@@ -927,11 +997,11 @@ k_project_tc(const __grid_constant__ TcParams prm) {
   tc_body<TF32, LEVELS, NPROD, false, 1, true>(prm);
 }
 
-template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C>
+template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C, bool F16 = false>
 cudaError_t launch_variant(const TcParams& prm, int grid, cudaStream_t s) {
-  using Lay = TcLayout<TF32, LEVELS>;
+  using Lay = TcLayout<TF32, LEVELS, F16>;
   const size_t smem = (size_t)Lay::kStages * Lay::kStageBytes;
-  auto kern = k_contract_tc<TF32, LEVELS, NPROD, CHECKS, C>;
+  auto kern = k_contract_tc<TF32, LEVELS, NPROD, CHECKS, C, F16>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (C == 1) {
@@ -973,6 +1043,13 @@ cudaError_t launch_projection(const TcParams& prm, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The FP16 form: two pieces, three products, no clusters.
+cudaError_t launch_form_f16(const TcParams& prm, int cluster, int grid, cudaStream_t s) {
+  if (cluster != 1) return cudaErrorInvalidValue;
+  if (prm.checks) return launch_variant<false, 2, 3, true, 1, true>(prm, grid, s);
+  return launch_variant<false, 2, 3, false, 1, true>(prm, grid, s);
+}
+
 template <bool TF32, int LEVELS, int NPROD>
 cudaError_t launch_form(const TcParams& prm, int cluster, int grid, cudaStream_t s) {
   if (prm.checks) {
@@ -993,6 +1070,13 @@ __global__ void k_reduce_slabs_f32(const TcJob* __restrict__ jobs, int n_slab, i
                                    int checks, unsigned long long* dbg, int* status) {
   const TcJob& J = jobs[blockIdx.y];
   const long long per = (long long)P_total * J.nd1 * J.nd2 * J.nd3;
+  // FP16 form: the partials carry the operands' power-of-two scales 2^(eA + eB)
+  double unscale = 1.0;
+  if (J.amax) {
+    int eA, eB;
+    f16_scale_exps(J.amax, eA, eB);
+    unscale = __longlong_as_double((long long)(1023 - eA - eB) << 52);   // 2^-(eA + eB)
+  }
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per;
        e += (long long)gridDim.x * blockDim.x) {
     double sr = 0.0, si = 0.0;
@@ -1001,7 +1085,7 @@ __global__ void k_reduce_slabs_f32(const TcJob* __restrict__ jobs, int n_slab, i
       sr += (double)v.x;
       si += (double)v.y;
     }
-    J.B[e] = make_double2(sr, si);
+    J.B[e] = make_double2(sr * unscale, si * unscale);
   }
   (void)checks; (void)dbg; (void)status;  // every index above is below n_slab * per or per
 }
@@ -1009,6 +1093,7 @@ __global__ void k_reduce_slabs_f32(const TcJob* __restrict__ jobs, int n_slab, i
 }  // namespace
 
 int tc_groups_per_stage(int form) { return form == TC_TF32_3 ? 8 : 16; }
+bool tc_form_needs_amax(int form) { return form == TC_F16_3; }
 
 cudaError_t launch_contract_tc(const TcParams& prm, int form, int cluster, int grid,
                                cudaStream_t s) {
@@ -1020,6 +1105,7 @@ cudaError_t launch_contract_tc(const TcParams& prm, int form, int cluster, int g
     case TC_BF16_6: return launch_form<false, 3, 6>(prm, cluster, grid, s);
     case TC_BF16_9: return launch_form<false, 3, 9>(prm, cluster, grid, s);
     case TC_TF32_3: return launch_form<true, 2, 3>(prm, cluster, grid, s);
+    case TC_F16_3: return launch_form_f16(prm, cluster, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -102,7 +102,7 @@ def test_a_line_without_dilution_columns_is_rejected(env):
 
 
 FORMS = [("fp64", 6, 1e-12), ("df64", 6, 1e-12), ("bf16", 6, 1e-6), ("tf32x3", 6, 1e-6),
-         ("bf16", 3, 1e-4)]
+         ("bf16", 3, 1e-4), ("fp16x3", 6, 1e-6)]
 
 
 @pytest.mark.parametrize("form", range(len(FORMS)))

@@ -14,6 +14,10 @@ in its default launch configuration: default tiles, CUDA graphs on a created str
   time slices per noise triple: 12 jobs of uneven size in one batched call, in the mixed
   forms and the double-float form. The call is repeated, so the second call is a
   CUDA-graph capture and the third a replay; every call is checked.
+* The same workload at its full size, all 48 time slices: 288 jobs in one batched call, in
+  the benchmark's headline form and launch configuration. The default workspace budget
+  splits it into several waves; the second call is captured and the third replayed, and
+  both are checked on jobs spread over every wave.
 
 Tolerances are relative Frobenius errors over the sampled entries: 1e-12 for the FP64 and
 double-float forms, 1e-6 for the split forms with 6 or 9 BF16 products and for TF32x3, and
@@ -30,7 +34,8 @@ pytestmark = pytest.mark.gpu
 
 FORMS = {"fp64": ("fp64", 6, 1e-12), "df64": ("df64", 6, 1e-12),
          "bf16x6": ("bf16", 6, 1e-6), "bf16x9": ("bf16", 9, 1e-6),
-         "tf32x3": ("tf32x3", 6, 1e-6), "bf16x3": ("bf16", 3, 1e-4)}
+         "tf32x3": ("tf32x3", 6, 1e-6), "bf16x3": ("bf16", 3, 1e-4),
+         "fp16x3": ("fp16x3", 6, 1e-6)}
 
 
 @pytest.fixture(scope="module")
@@ -86,7 +91,7 @@ def test_l32_nev128_ndil64_sampled(env, l32_inputs, form):
         assert err <= tol
 
 
-@pytest.mark.parametrize("form", ["fp64", "df64", "bf16x6"])
+@pytest.mark.parametrize("form", ["fp64", "df64", "bf16x6", "fp16x3"])
 def test_l48_nev264_ndil64_sampled(env, form):
     torch, bb = env
     precision, products, tol = FORMS[form]
@@ -110,7 +115,7 @@ def test_l48_nev264_ndil64_sampled(env, form):
     assert err <= tol
 
 
-@pytest.mark.parametrize("form", ["bf16x6", "tf32x3", "df64"])
+@pytest.mark.parametrize("form", ["bf16x6", "tf32x3", "df64", "fp16x3"])
 def test_l32_batch_uneven_dilution_sampled(env, form):
     torch, bb = env
     precision, products, tol = FORMS[form]
@@ -151,4 +156,54 @@ def test_l32_batch_uneven_dilution_sampled(env, form):
             worst = max(worst, err)
             assert err <= tol, (call, k, t, err)
         print(f"{form} batch call {call}: worst sampled rel. error {worst:.3e}")
+    bb.bblock_destroy(ctx)
+
+
+@pytest.mark.parametrize("form", ["bf16x6", "fp16x3"])
+def test_l32_full_batch_every_wave_sampled(env, form):
+    torch, bb = env
+    precision, products, tol = FORMS[form]
+    w = workloads.WORKLOADS["l32_batch_48t_6noise"]
+    inp = workloads.generate(w)
+    n_t = inp.V.shape[0]
+    assert n_t == 48 and len(inp.ndil) == 6
+    dev = torch.device("cuda:0")
+    V = torch.from_numpy(inp.V).to(dev)
+    jobs, outs = [], []
+    for k in range(w.n_noise):
+        phis = [torch.from_numpy(inp.phi[k][i]).to(dev) for i in range(3)]
+        Bk = torch.empty((n_t, len(inp.momenta), *inp.ndil[k]), dtype=torch.complex128, device=dev)
+        outs.append(Bk)
+        for t in range(n_t):
+            jobs.append((V[t], phis[0][t], phis[1][t], phis[2][t], Bk[t]))
+    n = len(jobs)
+    # 16 jobs spread evenly over the job list (noise-major), first and last included
+    picks = sorted({round(i * (n - 1) / 15) for i in range(16)})
+    refs = {}
+    for j in picks:
+        k, t = divmod(j, n_t)
+        nd = inp.ndil[k]
+        ds = (samples(nd[0]), samples(nd[1]), samples(nd[2]))
+        refs[k, t] = (ds, oracle.bblock_sampled(w.L, inp.V[t], *[inp.phi[k][i][t] for i in range(3)],
+                                                inp.momenta, inp.spins, inp.coeffs, *ds))
+    ctx = bb.bblock_create(w.L, w.n_ev, max(max(nd) for nd in inp.ndil), precision,
+                           bf16_products=products)
+    stream = torch.cuda.Stream()
+    for call in range(3):           # plain launches, graph capture + replay, replay
+        with torch.cuda.stream(stream):
+            for Bk in outs:
+                Bk.fill_(float("nan"))
+        bb.bblock_compute_batch(ctx, jobs, inp.momenta, inp.spins, inp.coeffs, stream=stream)
+        waves = bb.bblock_last_wave_count(ctx)
+        bb.bblock_status(ctx)
+        stream.synchronize()
+        assert waves >= 3, waves
+        worst = 0.0
+        for (k, t), (ds, ref) in refs.items():
+            got = outs[k][t].cpu().numpy()
+            err = rel(sampled(got, *ds), ref)
+            worst = max(worst, err)
+            assert err <= tol, (call, k, t, err)
+        print(f"{form} full batch call {call}: {waves} waves, worst sampled rel. error "
+              f"{worst:.3e} over {len(refs)} jobs")
     bb.bblock_destroy(ctx)

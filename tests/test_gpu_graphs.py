@@ -34,7 +34,8 @@ def setup(torch, inp):
     return (torch.from_numpy(inp.V).to(dev), [torch.from_numpy(inp.phi[0][i]).to(dev) for i in range(3)])
 
 
-@pytest.mark.parametrize("precision,products", [("fp64", 6), ("df64", 6), ("bf16", 6), ("tf32x3", 6)])
+@pytest.mark.parametrize("precision,products", [("fp64", 6), ("df64", 6), ("bf16", 6), ("tf32x3", 6),
+                                                ("fp16x3", 6)])
 def test_graph_replay_is_bitwise_equal_to_plain_launches(env, precision, products):
     torch, bb = env
     inp = workloads.custom(4, 10, (9, 8, 12), 2, [(0, 0, 0), (1, 0, 0), (1, 1, 0)],
@@ -121,7 +122,7 @@ def test_bad_option_values_are_rejected(env):
 
 
 @pytest.mark.parametrize("precision,products,tol", [("fp64", 6, 1e-12), ("df64", 6, 1e-12), ("bf16", 6, 1e-6),
-                                                    ("tf32x3", 6, 1e-6)])
+                                                    ("tf32x3", 6, 1e-6), ("fp16x3", 6, 1e-6)])
 def test_multi_wave_batch_graph_replay(env, precision, products, tol):
     """A batch that runs as several waves of launches (a small workspace budget per wave),
     with mixed dilution sizes, captured and replayed: each wave's table copy in the graph
@@ -173,3 +174,38 @@ def test_multi_wave_batch_graph_replay(env, precision, products, tol):
         assert n == (n_plain if call == 0 else n_plain - 1)   # phase table cached after call 0
     for c in (one_wave, plain, ctx):
         bb.bblock_destroy(c)
+
+
+@pytest.mark.parametrize("precision,products", [("fp64", 6), ("bf16", 6), ("fp16x3", 6)])
+def test_launch_timing_covers_graph_replays(env, precision, products):
+    """With launch timing on, the captured graph carries the timing events, so replays are
+    timed launch by launch: every replay adds its launches to the per-kernel totals, and
+    the replayed blocks stay bitwise those of the plain launches."""
+    torch, bb = env
+    inp = workloads.custom(4, 10, (9, 8, 12), 2, [(0, 0, 0), (1, 0, 0)],
+                           [(0, 1, 0), (1, 0, 0)], [0.7, -0.7], seed=3100)
+    V, phis = setup(torch, inp)
+    ctx = bb.bblock_create(4, 10, 12, precision, bf16_products=products)
+    stream = torch.cuda.Stream()
+    B = torch.empty((2, 2, 9, 8, 12), dtype=torch.complex128, device="cuda:0")
+    bb.bblock_profile_enable(ctx, True)
+    outs = []
+    for call in range(5):      # plain, capture + first replay, three replays
+        bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B,
+                          stream=stream)
+        bb.bblock_status(ctx)
+        outs.append(B.cpu().numpy())
+        if call == 0:
+            n_plain = bb.bblock_last_launch_count(ctx) - 1     # without the phase table
+            bb.bblock_profile_read(ctx)                        # reset
+    prof = bb.bblock_profile_read(ctx)
+    bb.bblock_profile_enable(ctx, False)
+    assert sum(v[0] for v in prof.values()) == 4 * n_plain, prof
+    assert prof["contract"][0] >= 4 and all(v[1] > 0 for v in prof.values())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    ref = oracle.bblock(4, inp.V[0], *[inp.phi[0][i][0] for i in range(3)], inp.momenta,
+                        inp.spins, inp.coeffs)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert rel(outs[-1][0], ref) <= tol
+    bb.bblock_destroy(ctx)

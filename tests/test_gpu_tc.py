@@ -2,7 +2,8 @@
 the CPU FP64 oracle, through the C ABI.
 
 Tolerances (relative Frobenius error of the whole block set):
-  * BF16 split with 6 or 9 piece products, TF32 split with 3: <= 1e-6;
+  * BF16 split with 6 or 9 piece products, TF32 split with 3, FP16 split with 3 (operands
+    scaled into FP16's range by powers of two): <= 1e-6;
   * BF16 split with 3 piece products: <= 1e-4 (the dropped products are ~3 * 2^-16
     relative, so this form is reported, not claimed at 1e-6).
 """
@@ -16,8 +17,9 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 
-FORMS = [("bf16", 6, 1e-6), ("bf16", 9, 1e-6), ("tf32x3", 6, 1e-6), ("bf16", 3, 1e-4)]
-FORM_IDS = ["bf16x6", "bf16x9", "tf32x3", "bf16x3"]
+FORMS = [("bf16", 6, 1e-6), ("bf16", 9, 1e-6), ("tf32x3", 6, 1e-6), ("bf16", 3, 1e-4),
+         ("fp16x3", 6, 1e-6)]
+FORM_IDS = ["bf16x6", "bf16x9", "tf32x3", "bf16x3", "fp16x3"]
 
 
 @pytest.fixture(scope="module")
@@ -82,7 +84,7 @@ def test_small_shapes_against_oracle(env, form, case):
     assert err <= tol
 
 
-@pytest.mark.parametrize("form", [0, 2], ids=["bf16x6", "tf32x3"])
+@pytest.mark.parametrize("form", [0, 2, 4], ids=["bf16x6", "tf32x3", "fp16x3"])
 def test_momentum_dependent_coefficients(env, form):
     torch, bb = env
     precision, products, tol = FORMS[form]
@@ -129,7 +131,7 @@ def test_batch_with_uneven_dilution(env):
     bb.bblock_destroy(ctx)
 
 
-@pytest.mark.parametrize("form", [0, 2, 3], ids=["bf16x6", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("form", [0, 2, 3, 4], ids=["bf16x6", "tf32x3", "bf16x3", "fp16x3"])
 def test_l24_nev96_ndil32_sampled(env, form):
     """The benchmarked workload at full size in the mixed forms: sampled entries vs oracle."""
     torch, bb = env
@@ -145,3 +147,34 @@ def test_l24_nev96_ndil32_sampled(env, form):
         err = rel(sub, ref)
         print(f"{FORM_IDS[form]} L=24 t={t}: sampled rel. error {err:.3e}")
         assert err <= tol
+
+
+@pytest.mark.parametrize("scales", [(2.0 ** 40, 2.0 ** -30, 2.0 ** 20),
+                                    (2.0 ** -50, 2.0 ** -45, 2.0 ** -40),
+                                    (1e20, 1e15, 1e-20)], ids=["mixed", "tiny", "wide"])
+def test_fp16_form_scales_operands_into_range(env, scales):
+    """The FP16 form holds 1e-6 whatever the magnitude of the inputs. Each quark line's
+    coefficients are scaled by a factor far outside FP16's range (largest finite 65504,
+    smallest normal 2^-14); the blocks must be the oracle's blocks of the scaled inputs,
+    because the operands are brought into range by powers of two chosen per job."""
+    torch, bb = env
+    inp = workloads.custom(5, 12, (12, 11, 13), 2, [(0, 0, 0), (1, 0, 0), (1, 1, 0)],
+                           [(0, 1, 0), (1, 0, 0), (2, 3, 2)], [0.7, -0.7, 0.7], seed=2400)
+    for i in range(3):
+        inp.phi[0][i] *= scales[i]
+    got = gpu_blocks(torch, bb, inp, "fp16x3", 6)
+    ref = oracle_blocks(inp)
+    err = rel(got, ref)
+    print(f"fp16x3 scales {scales}: rel. Frobenius error {err:.3e}")
+    assert np.all(np.isfinite(got)) and err <= 1e-6
+
+
+def test_fp16_form_zero_line_gives_zero_blocks(env):
+    """A quark line that is identically zero has no largest entry to scale by: the blocks
+    are exactly zero, not NaN."""
+    torch, bb = env
+    inp = workloads.custom(4, 8, (8, 9, 10), 1, [(0, 0, 0), (1, 0, 0)],
+                           [(0, 1, 0), (1, 0, 0)], [0.5, -0.5], seed=2500)
+    inp.phi[0][2][:] = 0.0
+    got = gpu_blocks(torch, bb, inp, "fp16x3", 6)
+    assert np.array_equal(got, np.zeros_like(got))

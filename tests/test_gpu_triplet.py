@@ -33,7 +33,8 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("precision,products,tol", [("fp64", 6, 1e-12), ("df64", 6, 1e-12),
-                                                    ("bf16", 6, 1e-6), ("tf32x3", 6, 1e-6)])
+                                                    ("bf16", 6, 1e-6), ("tf32x3", 6, 1e-6),
+                                                    ("fp16x3", 6, 1e-6)])
 def test_mode_triplet_matches_eq4(env, precision, products, tol):
     torch, bb = env
     mom = [(0, 0, 0), (1, 0, 0), (-1, 1, 2)]

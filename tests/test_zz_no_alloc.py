@@ -70,10 +70,43 @@ def test_two_calls_in_a_row_match_the_regular_entry_point(env):
         bb.bblock_contract_noalloc(L, *qs, inp.momenta, inp.spins, inp.coeffs, B)
         outs.append(B)
     torch.cuda.synchronize()
-    for k, ((_, _, ref), B) in enumerate(zip(prepared, outs)):
+    for k, ((inp, _, ref), B) in enumerate(zip(prepared, outs)):
         got = B.cpu().numpy()
         assert np.isfinite(got).all(), f"call {k}"
         assert rel(got, ref) <= TOL_FP64, f"call {k}"
+        # and against the oracle directly
+        ref_o = oracle.bblock(inp.workload.L, inp.V[0], *[inp.phi[0][i][0] for i in range(3)],
+                              inp.momenta, inp.spins, inp.coeffs)
+        assert rel(got, ref_o) <= TOL_FP64, f"call {k}"
+
+
+def test_request_that_fills_the_static_scratch(env):
+    """Shapes whose blocks fill the fixed scratch exactly (one slab of partial sums) or half
+    of it (two slabs): the slab count is capped by the scratch, and the blocks still match
+    the regular entry point. Two calls in a row again, the larger first."""
+    torch, bb = env
+    dev = torch.device("cuda:0")
+    L, n_ev, nd = 2, 6, (64, 64, 64)
+    spins, coeffs = [(0, 1, 0), (1, 0, 2)], [0.6, -0.8j]
+    moms = [[(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1),
+             (1, 1, 1)],                                    # 8 * 64^3 * 16 B = 32 MiB
+            [(0, 0, 0), (1, 0, 0), (0, 1, 1), (1, 1, 1)]]   # 16 MiB: two slabs fit
+    for k, mom in enumerate(moms):
+        assert len(mom) * 64 ** 3 * 16 <= 32 * 1024 * 1024
+        prepared = regular_entry_point(torch, bb, (L, n_ev, nd, mom, spins, coeffs), seed=600 + k)
+        inp, qs, ref = prepared
+        B = torch.full((len(mom), *nd), complex(np.nan, np.nan), dtype=torch.complex128,
+                       device=dev)
+        bb.bblock_contract_noalloc(L, *qs, inp.momenta, inp.spins, inp.coeffs, B)
+        torch.cuda.synchronize()
+        got = B.cpu().numpy()
+        assert np.isfinite(got).all(), f"case {k}"
+        assert rel(got, ref) <= TOL_FP64, f"case {k}"
+        # and against the oracle directly, on sampled entries
+        d = [0, 31, 63]
+        ref_o = oracle.bblock_sampled(L, inp.V[0], *[inp.phi[0][i][0] for i in range(3)],
+                                      inp.momenta, inp.spins, inp.coeffs, d, d, d)
+        assert rel(got[:, d][:, :, d][:, :, :, d], ref_o) <= TOL_FP64, f"case {k}"
 
 
 def test_requests_beyond_the_static_scratch_are_rejected(env):
