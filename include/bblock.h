@@ -192,7 +192,8 @@ int bblock_last_wave_count(const bblock_ctx* ctx);
                                   created stream (not the legacy or per-thread default
                                   stream) is captured as a CUDA graph on its second
                                   occurrence and replayed afterwards; 0: plain launches */
-#define BBLOCK_OPT_TC_NC 2     /* tensor-core forms: complex columns per tile, 16, 32 or 48 */
+#define BBLOCK_OPT_TC_NC 2     /* tensor-core forms: complex columns per tile, 16, 32 or 48;
+                                  the FP16 form's CTA pairs also take 64 or 80 */
 #define BBLOCK_OPT_TC_CHUNK 3  /* tensor-core forms: stages between accumulator drains, 1..8 */
 #define BBLOCK_OPT_SLABS 4     /* site slabs per job (split of the site sum), 1..4096 */
 #define BBLOCK_OPT_CHECKS 5    /* 1: the tensor-core contraction checks every global index
@@ -213,8 +214,12 @@ int bblock_last_wave_count(const bblock_ctx* ctx);
                                        sharing each 128-pair diquark tile, 2, 4 or 8 (each
                                        builds 1/C of it and takes its own N tile; results are
                                        bitwise those of the plain kernel with the same tiles);
-                                       0 (default) or 1: no clusters. Index checks and the
-                                       wait-limit test hook use no clusters */
+                                       0 (default) or 1: no clusters. FP16 form: 1 runs plain
+                                       CTAs with N tiles of up to 48 columns; any other value
+                                       (the default) runs CTA pairs that share the third-quark
+                                       tile of an N tile of up to 80 columns and take adjacent
+                                       128-pair tiles. Index checks and the wait-limit test
+                                       hook use no clusters */
 #define BBLOCK_OPT_CORRUPT_CANARY 9  /* test hook (with BBLOCK_OPT_CHECKS): 1 makes the next
                                        call overwrite its first canary from the host, in
                                        stream order between the fill and the check, once */
@@ -309,6 +314,16 @@ int bblock_costmodel_train(bblock_costmodel* model, const float* X, const float*
                            int epochs, float lr, float* final_loss);
 /* Predictions y [n] for X [n][F] (host buffers). */
 int bblock_costmodel_predict(bblock_costmodel* model, const float* X, int n, float* y);
+
+/* ---------------------------------------------------------------- FP64 throughput probe
+ * Not in the paper. Measures the two FP64 paths of `device`: scalar fused multiply-adds
+ * (DFMA, which the FP64 form's kernels use) and the FP64 tensor-core MMA (mma.sync
+ * m8n8k4 f64), each as the best of three timed launches of register-resident loops over
+ * every SM, in TFLOP/s (2 flops per FMA). The FP64 form's roofline takes the measured DFMA
+ * rate as its peak. Allocates 16 bytes of device memory and two events for the duration of
+ * the call; synchronises `stream`. Returns BBLOCK_ERR_INVALID_ARG (bad device or NULL
+ * outputs) or BBLOCK_ERR_CUDA. */
+int bblock_probe_fp64(int device, double* dfma_tflops, double* dmma_tflops, void* stream);
 
 /* Size of the fixed device scratch used by bblock_contract_noalloc (32 MiB). */
 #define BBLOCK_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)

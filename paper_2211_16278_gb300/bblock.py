@@ -38,7 +38,7 @@ EXPORTED = (
     "bblock_costmodel_create", "bblock_costmodel_destroy", "bblock_costmodel_num_params",
     "bblock_costmodel_get_params", "bblock_costmodel_set_params", "bblock_costmodel_gradient",
     "bblock_costmodel_train", "bblock_costmodel_predict", "bblock_mode_triplet",
-    "bblock_from_triplet",
+    "bblock_from_triplet", "bblock_probe_fp64",
 )
 TUNE_FEATURES = 12
 OPTIONS = {"graphs": 1, "tc_nc": 2, "tc_chunk": 3, "slabs": 4, "checks": 5, "wave_mb": 6,
@@ -112,6 +112,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bblock_last_launch_count.restype = I
     lib.bblock_last_wave_count.argtypes = [P]
     lib.bblock_last_wave_count.restype = I
+    lib.bblock_probe_fp64.argtypes = [I, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), P]
+    lib.bblock_probe_fp64.restype = I
     lib.bblock_profile_enable.argtypes = [P, I]
     lib.bblock_profile_enable.restype = I
     lib.bblock_profile_read.argtypes = [P, ctypes.POINTER(bblock_kernel_stat), I,
@@ -202,6 +205,15 @@ def bblock_last_launch_count(ctx: Context) -> int:
 
 def bblock_last_wave_count(ctx: Context) -> int:
     return int(load().bblock_last_wave_count(ctx.handle))
+
+
+def bblock_probe_fp64(device: int = 0, stream=None) -> dict:
+    """Measured FP64 rates of the device: {"dfma_tflops": .., "dmma_tflops": ..}."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = load().bblock_probe_fp64(device, ctypes.byref(a), ctypes.byref(b),
+                                  _stream_handle(stream))
+    _check(None, rc)
+    return {"dfma_tflops": a.value, "dmma_tflops": b.value}
 
 
 def bblock_set_option(ctx: Context, option: str, value: int) -> None:

@@ -454,8 +454,9 @@ int tc_form_of(const bblock_config& cfg) {
 // Complex columns per tensor-core tile: the N tile that wastes the fewest padded columns,
 // counting a fixed per-tile cost of 16 columns for building the shared diquark tile.
 struct TcTiling {
-  int cluster = 1;  // CTAs sharing one diquark tile (1: none)
-  int nc = 48;      // complex (p, d3) columns per CTA
+  int cluster = 1;       // CTAs of a cluster (1: none)
+  int nc = 48;           // complex (p, d3) columns per CTA
+  bool share_b = false;  // cluster = 2 CTA pairs sharing the third-quark tile (FP16 form)
 };
 
 // Cluster size and N tile for jobs [b, e).
@@ -469,8 +470,32 @@ struct TcTiling {
 // N_dil = 64), 14 % slower for the 2-piece form, and unchanged at 96 or 320 columns;
 // clusters of 4 or 8 are slower, because the stage time barely falls with the diquark
 // work per CTA.
+//
+// FP16 form: CTA pairs that share the third-quark tile unless the caller asks for no
+// cluster, for index checks or for the wait-limit test hook. A pair builds 2 x 128 diquark
+// rows and NC third-quark rows per stage for an N tile of up to 80 columns, so the N tile
+// is the one with the least (256 + nc) x tiles over the wave's jobs.
 TcTiling choose_tc_tiling(const bblock_ctx* c, const std::vector<JobIn>& jobs, size_t b,
                           size_t e, int P, int form, int nc_fixed) {
+  if (form == TC_F16_3 && !c->opt_checks && c->opt_wait_us == 0 && c->opt_tc_cluster != 1) {
+    TcTiling pair;
+    pair.cluster = 2;
+    pair.share_b = true;
+    pair.nc = nc_fixed > 0 ? nc_fixed : 80;
+    if (nc_fixed <= 0) {
+      long long best_cost = -1;
+      for (int nc = tc_max_nc(form, true); nc >= 16; nc -= 16) {
+        long long cost = 0;
+        for (size_t k = b; k < e; ++k) {
+          const long long N = (long long)P * jobs[k].nd[2];
+          const long long mp = (((long long)jobs[k].nd[0] * jobs[k].nd[1] + 127) / 128 + 1) / 2;
+          cost += mp * ((N + nc - 1) / nc) * (nc + 256);
+        }
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; pair.nc = nc; }
+      }
+    }
+    return pair;
+  }
   const bool can_cluster = form != TC_TF32_3 && form != TC_F16_3 && !c->opt_checks &&
                            c->opt_wait_us == 0 && c->opt_tc_cluster != 1;
   TcTiling best;
@@ -533,13 +558,21 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     const int nj = (int)(end - job_idx);
     const TcTiling tt = choose_tc_tiling(c, jobs, job_idx, end, P_launch, form, c->opt_tc_nc);
     const int NC = tt.nc, CL = tt.cluster;
+    if (NC > tc_max_nc(form, tt.share_b))
+      return fail(c, BBLOCK_ERR_INVALID_ARG, "N tile of %d columns exceeds this form's %d", NC,
+                  tc_max_nc(form, tt.share_b));
+    // M tiles of 128 (d1, d2) pairs per unit (two adjacent ones for CTA pairs) and N tiles
+    // per unit (CL adjacent ones for clusters sharing the diquark tile)
+    auto unit_m_tiles = [&](const JobIn& j) -> long long {
+      const long long mt = ((long long)j.nd[0] * j.nd[1] + 127) / 128;
+      return tt.share_b ? (mt + 1) / 2 : mt;
+    };
+    const int n_group = tt.share_b ? NC : CL * NC;
     long long tiles = 0, max_elems = 0;
     int max_ndf = 0;
     for (size_t k = job_idx; k < end; ++k) {
       const JobIn& j = jobs[k];
-      // cluster units: one per (128-pair tile, group of CL N tiles)
-      tiles += (long long)((j.nd[0] * j.nd[1] + 127) / 128) *
-               ((P_launch * j.nd[2] + (long long)CL * NC - 1) / ((long long)CL * NC));
+      tiles += unit_m_tiles(j) * ((P_launch * j.nd[2] + (long long)n_group - 1) / n_group);
       for (int i = 0; i < 3; ++i) max_ndf = std::max(max_ndf, j.nd[i]);
       max_elems = std::max(max_elems, (long long)P_launch * j.nd[0] * j.nd[1] * j.nd[2]);
     }
@@ -627,9 +660,9 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       base += align_up((size_t)n_slab * P_launch * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(float2), 256);
       canary(base);
       ws = base;
-      const int m_tiles = (j.nd[0] * j.nd[1] + 127) / 128;           // (d1, d2) pairs
+      const int m_tiles = (int)unit_m_tiles(j);                       // (d1, d2) pairs
       // groups of CL N tiles of NC (p, d3) columns: a cluster unit covers one group
-      const int n_tiles = (P_launch * j.nd[2] + CL * NC - 1) / (CL * NC);
+      const int n_tiles = (P_launch * j.nd[2] + n_group - 1) / n_group;
       for (int set = 0; set < sp.n_coef_sets; ++set) {
         TcJob& tj = tjobs[set][k];
         for (int i = 0; i < 4; ++i) { tj.q1[i] = q1[i]; tj.q2[i] = q2[i]; }
@@ -730,6 +763,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     for (int pr = 0; pr < sp.n_pairs; ++pr) { prm.a_slot[pr] = sp.a_slot[pr]; prm.b_slot[pr] = sp.b_slot[pr]; }
     prm.P = P_launch;
     prm.NC = NC;
+    prm.share_b = tt.share_b ? 1 : 0;
     prm.chunk_stages = chunk_stages;
     prm.status = c->d_status;
     prm.checks = c->opt_checks;
@@ -1175,14 +1209,16 @@ CallPlan plan_call(const bblock_ctx* c, int n_t, const int nd[3], int n_mom, int
   const TcTiling tt = choose_tc_tiling(c, one, 0, 1, n_mom, tc_form_of(c->cfg), nc_opt);
   pl.nc = tt.nc;
   const long long N = (long long)n_mom * nd[2];                   // (p, d3) columns
-  const long long n_tiles = (N + (long long)tt.cluster * pl.nc - 1) / ((long long)tt.cluster * pl.nc);
-  const long long tiles = (long long)n_t * (((long long)nd[0] * nd[1] + 127) / 128) * n_tiles;
+  const long long n_group = tt.share_b ? pl.nc : (long long)tt.cluster * pl.nc;
+  const long long n_tiles = (N + n_group - 1) / n_group;
+  const long long mt = ((long long)nd[0] * nd[1] + 127) / 128;
+  const long long tiles = (long long)n_t * (tt.share_b ? (mt + 1) / 2 : mt) * n_tiles;
   int ns = slabs_opt > 0 ? std::max(min_slabs, std::min(slabs_opt, X))
                          : std::max(min_slabs, choose_slabs(tiles, c->num_sms / tt.cluster, X, 1, max_slabs));
   const int sps = (X + ns - 1) / ns;
   pl.n_slab = (X + sps - 1) / sps;
   pl.units = tiles * pl.n_slab;
-  pl.pad = (double)(n_tiles * tt.cluster * pl.nc) / N - 1.0;
+  pl.pad = (double)(n_tiles * n_group) / N - 1.0;
   return pl;
 }
 
@@ -1642,7 +1678,10 @@ int bblock_autotune(bblock_ctx* c, int n_t, const void* V, const void* phi1, con
   if (fp64_like(c->cfg)) {
     for (int k = 0; k < 4; ++k) cand.push_back({0, 0, slab_choices[k]});
   } else {
-    for (int nc = 16; nc <= 48; nc += 16)
+    const int form = tc_form_of(c->cfg);
+    const bool pairs_on = form == TC_F16_3 && !c->opt_checks && c->opt_wait_us == 0 &&
+                          c->opt_tc_cluster != 1;
+    for (int nc = 16; nc <= tc_max_nc(form, pairs_on); nc += 16)
       for (int ch = 1; ch <= 3; ++ch)
         for (int k = 0; k < 3; ++k) cand.push_back({nc, ch, slab_choices[k]});
   }
@@ -1737,7 +1776,9 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       if (!value) drop_graph(c);
       return BBLOCK_OK;
     case BBLOCK_OPT_TC_NC:
-      if (value != 0 && value != 16 && value != 32 && value != 48) break;
+      if (value != 0 && value != 16 && value != 32 && value != 48 &&
+          !(c->cfg.precision == BBLOCK_FP16X3 && (value == 64 || value == 80)))
+        break;
       c->opt_tc_nc = value;
       return BBLOCK_OK;
     case BBLOCK_OPT_TC_CHUNK:

@@ -120,8 +120,11 @@ struct TcParams {
   int b_slot[kMaxPairs];
   const float2* phase;           // [P][X], the FP64 phases rounded to FP32
   int P;                         // momenta (columns n = p*nd3 + d3)
-  int NC;                        // complex columns per tile: 16, 32 or 48
+  int NC;                        // complex columns per tile: 16, 32 or 48 (up to 80 in pairs)
   int chunk_stages;              // stages accumulated in TMEM between drains
+  // CTA pairs (FP16 form, cluster = 2): the two CTAs of a cluster share the third-quark tile
+  // of one N tile and take adjacent M tiles; a job's m_tiles then counts pairs of M tiles
+  int share_b;
   int* status;
   // index checks (debug option): every global access is checked against its buffer; the
   // first violation is recorded in dbg[0..3] = (site code, job, index, bound) and skipped
@@ -160,6 +163,8 @@ cudaError_t launch_project_tc(const TcParams& p, int form, int grid, cudaStream_
 int tc_groups_per_stage(int form);
 // true for the forms that scale their operands from the fields' maxima (TcJob::amax)
 bool tc_form_needs_amax(int form);
+// widest N tile (complex columns) of a form, plain CTAs or CTA pairs sharing the B tile
+int tc_max_nc(int form, bool share_b);
 cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab, int P_total,
                                     long long max_elems, int checks, unsigned long long* dbg,
                                     int* status, cudaStream_t s);

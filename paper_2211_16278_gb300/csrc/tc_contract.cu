@@ -78,7 +78,6 @@ constexpr long long kWaitCycles = 4000000000LL;  // about 2 s: the default limit
 constexpr long long kDrainCycles = 20000000LL;   // about 10 ms: abort-path drain of peer copies
 constexpr int kBarProd = 1, kBarEpi = 2;
 constexpr int kAPlaneBytes = kTcM * 96;          // 128 rows x 96 bytes of K per stage
-constexpr int kBPlaneBytes = kMaxNC * 96;        // room for one plane of up to 48 rows
 // The third-quark operand of each piece level holds three planes, -Bi | Br | Bi, each of NC
 // rows (NC * 96 bytes, so that consecutive planes continue one another's 8-row groups).
 // Then [Br | Bi] and [-Bi | Br] are both contiguous operands of 2 NC rows, and a complex
@@ -89,13 +88,17 @@ constexpr int kBPlaneBytes = kMaxNC * 96;        // room for one plane of up to 
 // The 2-piece BF16 form, bound by its producers, loses 2-4 % to the extra -Bi stores and
 // the larger stages (less L1 for the producers' loads): it keeps two planes, Br | Bi, and
 // four MMAs of N = NC.
-template <bool TF32, int LEVELS, bool F16 = false> struct TcLayout {
+// WIDE (the CTA-pair form): N tiles of up to kMaxNCWide complex columns, two stages.
+template <bool TF32, int LEVELS, bool F16 = false, bool WIDE = false> struct TcLayout {
   static constexpr bool kTwoMma = TF32 || LEVELS == 3 || F16;
   static constexpr int kBPlanes = kTwoMma ? 3 : 2;
   static constexpr int kBr = kTwoMma ? 1 : 0, kBi = kBr + 1;   // plane slots; -Bi is slot 0
-  static constexpr int kStages = LEVELS == 3 ? 2 : 3;
-  static constexpr int kStageBytes = LEVELS * (2 * kAPlaneBytes + kBPlanes * kBPlaneBytes);
+  static constexpr int kMaxCols = WIDE ? 80 : kMaxNC;          // complex columns per N tile
+  static constexpr int kBPlaneB = kMaxCols * 96;               // bytes of one B plane
+  static constexpr int kStages = (LEVELS == 3 || WIDE) ? 2 : 3;
+  static constexpr int kStageBytes = LEVELS * (2 * kAPlaneBytes + kBPlanes * kBPlaneB);
 };
+constexpr int kMaxNCWide = 80;
 constexpr int kSegsPerRow = 6;                   // 16-byte core-matrix columns per row
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -445,23 +448,33 @@ __device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t parity,
 // with m = (site, colour) and Phi the coefficient-folded phi columns of one field; the same
 // pipeline with the K index of a stage read as the eigenvector index
 // l = stage * 3G + colour * G + group, and the unit's sum written as the FP32 field.
-template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C, bool PROJ, bool F16 = false>
+//
+// SHB (C = 2, the FP16 form): the CTA pair form. Both CTAs of a cluster take the same
+// (job, N tile, slab) and adjacent 128-row M tiles; each builds its own diquark rows and
+// half of the third-quark rows, and pushes that half into the peer's stage (bulk
+// shared::cta -> shared::cluster copies counted on the peer's stage barrier). Each CTA
+// then runs its own MMAs on its diquark rows and the whole third-quark tile, which can be
+// up to 80 complex columns wide because the accumulators are single-buffered there.
+template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C, bool PROJ, bool F16 = false,
+          bool SHB = false>
 __device__ __forceinline__ void tc_body(const TcParams& prm) {
-  using R = Roles<TF32, C>;
+  using R = Roles<TF32, SHB ? 1 : C>;
   static_assert(!PROJ || (C == 1 && !CHECKS), "the projection runs without clusters or checks");
-  static_assert(!F16 || (!TF32 && LEVELS == 2 && C == 1 && !PROJ),
-                "the FP16 form: two pieces, no cluster, contraction only");
+  static_assert(!F16 || (!TF32 && LEVELS == 2 && (C == 1 || SHB) && !PROJ),
+                "the FP16 form: two pieces, contraction only, clusters only as CTA pairs");
+  static_assert(!SHB || (F16 && C == 2 && !CHECKS), "CTA pairs: the FP16 form, unchecked");
+  constexpr bool kShareA = C > 1 && !SHB;          // cluster CTAs share the diquark tile
   constexpr int G = TF32 ? 8 : 16;                 // (site, pair) groups per stage
   // transaction bytes a stage receives from the peers: their diquark rows, every plane
   constexpr uint32_t kPeerTx = (uint32_t)((C - 1) * (R::kARows / 8) * 768 * LEVELS * 2);
-  using Lay = TcLayout<TF32, LEVELS, F16>;
+  using Lay = TcLayout<TF32, LEVELS, F16, SHB>;
   constexpr int STAGES = Lay::kStages;
   constexpr int STAGE_BYTES = Lay::kStageBytes;
   constexpr bool kTwoMma = Lay::kTwoMma;   // complex product as two N = 2 NC MMAs
   constexpr int kBPlanes = Lay::kBPlanes;
   // groups whose loads a producer thread issues together before computing: all 8 in one
-  // round where the registers allow it; the cluster and checked variants would spill
-  constexpr int kLoadRun = (C == 1 && !CHECKS) ? 8 : 4;
+  // round where the registers allow it; the A-sharing cluster and checked variants would spill
+  constexpr int kLoadRun = (!kShareA && !CHECKS) ? 8 : 4;
   auto decode = [&](long long u) -> Unit {
     if constexpr (PROJ) return decode_unit_proj(prm, u, 3 * G);
     else return decode_unit(prm, u, G);
@@ -483,6 +496,11 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int NC = prm.NC;
   const int np = prm.n_pairs;
+  // accumulator buffers: double-buffered [lead | corr] (4 NC columns each) and the FP32
+  // running sum (2 NC) while 10 NC <= 512 TMEM columns; single-buffered beyond
+  const int nbuf = 10 * NC <= kTmemCols ? 2 : 1;
+  // CTA pairs: transaction bytes of the peer's third-quark rows (NC / 2 rows, every plane)
+  const uint32_t peer_tx = SHB ? (uint32_t)((NC / 16) * LEVELS * Lay::kBPlanes * 768) : kPeerTx;
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -518,7 +536,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   // plane slots: -Bi = 0, Br = 1, Bi = 2 (two-MMA forms); Br = 0, Bi = 1 (the others)
   auto b_plane = [&](int stage, int level, int plane) -> uint32_t {
     return (uint32_t)(stage * STAGE_BYTES + LEVELS * 2 * kAPlaneBytes +
-                      level * kBPlanes * kBPlaneBytes + plane * NC * 96);
+                      level * kBPlanes * Lay::kBPlaneB + plane * NC * 96);
   };
   auto row_seg = [](int r, int seg) -> uint32_t {
     return (uint32_t)(((r >> 3) * kSegsPerRow + seg) * 128 + (r & 7) * 16);
@@ -533,8 +551,9 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
     const bool is_a = pt < R::kAThreads;
     const bool is_b = !is_a && pt < R::kAThreads + R::kBThreads;
     int rr, g0;
+    bool b_row_in = false;   // a third-quark row of this CTA's share
     if (is_a) {
-      if (C == 1) {
+      if (!kShareA) {
         rr = pt % kTcM;
         g0 = (pt / kTcM) * 8;
       } else {   // 8 rows x 4 items per warp: the warp's rows are one core-matrix row group
@@ -543,11 +562,19 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
       }
     } else {
       const int b = is_b ? pt - R::kAThreads : 0;
-      rr = b % kMaxNC;
-      g0 = (b / kMaxNC) * R::kBGroups;
+      if (SHB) {   // 16 rows x 2 halves per warp: two whole core-matrix row groups per warp
+        const int lr = (b / 32) * 16 + (lane & 15);
+        rr = (int)rank * (NC / 2) + lr;
+        g0 = (lane >> 4) * 8;
+        b_row_in = lr < NC / 2;
+      } else {
+        rr = b % kMaxNC;
+        g0 = (b / kMaxNC) * R::kBGroups;
+        b_row_in = rr < NC;
+      }
     }
     const int NG = is_a ? R::kAGroups : R::kBGroups;
-    const bool row_used = is_a || (is_b && rr < NC);
+    const bool row_used = is_a || (is_b && b_row_in);
     long long s_g = 0;
     for (long long u = u0; u < prm.total_units; u += du) {
       const Unit w = decode(u);
@@ -588,14 +615,14 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
           f16s = pow2f(is_a ? eA : eB);
         }
         if (is_a) {
-          // M side: diquark of the pair m = d1 * nd2 + d2
-          const int m = w.mt * kTcM + rr;
+          // M side: diquark of the pair m = d1 * nd2 + d2 (CTA pairs: M tile 2 mt + rank)
+          const int m = (SHB ? w.mt * 2 + (int)rank : w.mt) * kTcM + rr;
           row_ok = m < nd1 * nd2;
           const int d1 = row_ok ? m / nd2 : 0, d2 = row_ok ? m - d1 * nd2 : 0;
           off1 = d1; off2 = d2; s1 = nd1; s2 = nd2;
         } else {
           // N side: phase x third quark of the column n = p * nd3 + d3
-          const int n = (w.nt * C + (int)rank) * NC + rr;
+          const int n = (kShareA ? w.nt * C + (int)rank : w.nt) * NC + rr;
           row_ok = row_used && n < prm.P * nd3;
           const int p = row_ok ? n / nd3 : 0, d3 = row_ok ? n - p * nd3 : 0;
           off1 = d3; s1 = nd3; pidx = p;
@@ -783,7 +810,26 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          if (C > 1 && is_a && ok) {
+          if (SHB && is_b && ok) {
+            // this warp's third-quark row groups (16 rows of this CTA's share) of every
+            // plane go to the peer, at the same offsets of its stage
+            const uint32_t peer = rank ^ 1u;
+            const uint32_t mbar = map_to_rank(smem_u32(&bar_full[slot]), peer);
+            const int lr0 = ((pt - R::kAThreads) / 32) * 16;
+#pragma unroll
+            for (int gq = 0; gq < 2; ++gq) {
+              if (lr0 + 8 * gq >= NC / 2) break;
+              const uint32_t rg = (uint32_t)(((int)rank * (NC / 2) + lr0 + 8 * gq) >> 3);
+#pragma unroll
+              for (int l = 0; l < LEVELS; ++l)
+#pragma unroll
+                for (int pl = 0; pl < kBPlanes; ++pl) {
+                  const uint32_t src = smem_base + b_plane(slot, l, pl) + rg * 768u;
+                  copy_to_peer(map_to_rank(src, peer), src, 768u, mbar);
+                }
+            }
+          }
+          if (kShareA && is_a && ok) {
             // this warp's 8 diquark rows (one row group) of every plane go to every peer
             const uint32_t rg = (uint32_t)(rr >> 3);
             const uint32_t full_local = smem_u32(&bar_full[slot]);
@@ -800,7 +846,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
             }
           }
           if (C > 1 && pt == 0)
-            mbar_arrive_expect_tx(smem_u32(&bar_full[slot]), kPeerTx);
+            mbar_arrive_expect_tx(smem_u32(&bar_full[slot]), peer_tx);
           else
             mbar_arrive(smem_u32(&bar_full[slot]));
         }
@@ -822,12 +868,13 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
         const Unit w = decode(u);
         for (int st = 0; st < w.n_stages; ++st, ++s_g) {
           const int slot = (int)(s_g % STAGES);
-          const int buf = (int)(c_g & 1);
+          const int buf = (int)(c_g % nbuf);
           const bool chunk_first = (st % prm.chunk_stages) == 0;
           const bool chunk_last = (st % prm.chunk_stages) == prm.chunk_stages - 1 ||
                                   st == w.n_stages - 1;
-          if (chunk_first && c_g >= 2) {
-            if (!wait_bounded(smem_u32(&bar_acc_empty[buf]), (uint32_t)(((c_g >> 1) + 1) & 1),
+          // the chunk's accumulator buffer must have been drained (its previous use)
+          if (chunk_first && c_g >= nbuf) {
+            if (!wait_bounded(smem_u32(&bar_acc_empty[buf]), (uint32_t)(((c_g / nbuf) + 1) & 1),
                               &abort_flag, prm.status, prm.wait_limit)) { stop = true; break; }
           }
           if (!wait_bounded(smem_u32(&bar_full[slot]), (uint32_t)((s_g / STAGES) & 1),
@@ -845,7 +892,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
             for (int q = 0; q < NPROD; ++q) {
               const uint64_t ar = smem_desc(sa + (PI[q] * 2 + 0) * kAPlaneBytes + kofs);
               const uint64_t ai = smem_desc(sa + (PI[q] * 2 + 1) * kAPlaneBytes + kofs);
-              const uint32_t bl = sb + (uint32_t)(PJ[q] * kBPlanes * kBPlaneBytes);
+              const uint32_t bl = sb + (uint32_t)(PJ[q] * kBPlanes * Lay::kBPlaneB);
               const uint32_t d = q == 0 ? lead : corr;
               const uint32_t acc = (q <= 1) ? first : 1u;
               if constexpr (kTwoMma) {
@@ -893,16 +940,16 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
     // ------------------------------------------------------------ epilogue (TMEM lanes)
     const int row = warp * 32 + lane;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const uint32_t run_r = tmem + lane_base + (uint32_t)(8 * NC);
+    const uint32_t run_r = tmem + lane_base + (uint32_t)(nbuf * 4 * NC);
     long long c_g = 0;
     for (long long u = u0; u < prm.total_units; u += du) {
       const Unit w = decode(u);
       const int n_chunks = (w.n_stages + prm.chunk_stages - 1) / prm.chunk_stages;
       for (int ch = 0; ch < n_chunks; ++ch, ++c_g) {
-        const int buf = (int)(c_g & 1);
+        const int buf = (int)(c_g % nbuf);
         bool ok = !abort_flag;
         if (ok)
-          ok = wait_bounded(smem_u32(&bar_acc_full[buf]), (uint32_t)((c_g >> 1) & 1),
+          ok = wait_bounded(smem_u32(&bar_acc_full[buf]), (uint32_t)((c_g / nbuf) & 1),
                             &abort_flag, prm.status, prm.wait_limit);
         // the TMEM loads below are warp-collective: decide per warp
         ok = __all_sync(0xffffffffu, ok);
@@ -947,7 +994,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
         } else if (!PROJ && ok && ch == n_chunks - 1) {
           // unit done: write the FP32 running sum as this slab's partial block
           const TcJob& J = prm.jobs[w.job];
-          const int m = w.mt * kTcM + row;
+          const int m = (SHB ? w.mt * 2 + (int)rank : w.mt) * kTcM + row;
           const int M = J.nd1 * J.nd2, nd3 = J.nd3, Ntot = prm.P * nd3;
           for (int col = 0; col < NC; col += 16) {
             float vr[16], vi[16];
@@ -958,7 +1005,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
             if (m < M) {
 #pragma unroll
               for (int i = 0; i < 16; ++i) {
-                const int n = (w.nt * C + (int)rank) * NC + col + i;
+                const int n = (kShareA ? w.nt * C + (int)rank : w.nt) * NC + col + i;
                 if (n < Ntot) {
                   const int p = n / nd3, d3 = n - p * nd3;
                   const size_t pi = (((size_t)w.slab * prm.P + p) * M + m) * nd3 + d3;
@@ -991,6 +1038,12 @@ __global__ void __launch_bounds__(Roles<TF32, C>::kThreads, 1)
 k_contract_tc(const __grid_constant__ TcParams prm) {
   tc_body<TF32, LEVELS, NPROD, CHECKS, C, false, F16>(prm);
 }
+// The FP16 form as CTA pairs that share the third-quark tile (clusters of 2).
+__global__ void __launch_bounds__(Roles<false, 1>::kThreads, 1)
+k_contract_tc_pair(const __grid_constant__ TcParams prm) {
+  tc_body<false, 2, 3, false, 2, false, true, true>(prm);
+}
+
 template <bool TF32, int LEVELS, int NPROD>
 __global__ void __launch_bounds__(Roles<TF32, 1>::kThreads, 1)
 k_project_tc(const __grid_constant__ TcParams prm) {
@@ -1043,9 +1096,45 @@ cudaError_t launch_projection(const TcParams& prm, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// The FP16 form: two pieces, three products, no clusters.
+// The FP16 form as CTA pairs: grid = CTAs wanted (even), capped at the pairs that can be
+// resident at once.
+cudaError_t launch_pair(const TcParams& prm, int grid, cudaStream_t s) {
+  using Lay = TcLayout<false, 2, true, true>;
+  const size_t smem = (size_t)Lay::kStages * Lay::kStageBytes;
+  auto kern = k_contract_tc_pair;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(Roles<false, 1>::kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)grid);
+  int max_clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
+  if (e != cudaSuccess) return e;
+  if (max_clusters < 1) return cudaErrorInvalidConfiguration;
+  const long long want = (grid + 1) / 2;
+  cfg.gridDim = dim3((unsigned)(2 * (want < max_clusters ? want : max_clusters)));
+  e = cudaLaunchKernelEx(&cfg, kern, prm);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// The FP16 form: two pieces, three products; plain CTAs (with or without index checks), or
+// CTA pairs sharing the third-quark tile (cluster = 2, unchecked).
 cudaError_t launch_form_f16(const TcParams& prm, int cluster, int grid, cudaStream_t s) {
-  if (cluster != 1) return cudaErrorInvalidValue;
+  if (cluster == 2 && prm.share_b) {
+    if (prm.checks) return cudaErrorInvalidValue;
+    return launch_pair(prm, grid, s);
+  }
+  if (cluster != 1 || prm.share_b || prm.NC > kMaxNC) return cudaErrorInvalidValue;
   if (prm.checks) return launch_variant<false, 2, 3, true, 1, true>(prm, grid, s);
   return launch_variant<false, 2, 3, false, 1, true>(prm, grid, s);
 }
@@ -1093,13 +1182,16 @@ __global__ void k_reduce_slabs_f32(const TcJob* __restrict__ jobs, int n_slab, i
 }  // namespace
 
 int tc_groups_per_stage(int form) { return form == TC_TF32_3 ? 8 : 16; }
+int tc_max_nc(int form, bool share_b) { return form == TC_F16_3 && share_b ? kMaxNCWide : kMaxNC; }
 bool tc_form_needs_amax(int form) { return form == TC_F16_3; }
 
 cudaError_t launch_contract_tc(const TcParams& prm, int form, int cluster, int grid,
                                cudaStream_t s) {
   if (prm.total_units == 0) return cudaSuccess;
-  if (prm.NC < 16 || prm.NC > kMaxNC || prm.NC % 16 != 0 || prm.chunk_stages < 1)
+  const int max_nc = (form == TC_F16_3 && prm.share_b) ? kMaxNCWide : kMaxNC;
+  if (prm.NC < 16 || prm.NC > max_nc || prm.NC % 16 != 0 || prm.chunk_stages < 1)
     return cudaErrorInvalidValue;
+  if (prm.share_b && form != TC_F16_3) return cudaErrorInvalidValue;
   switch (form) {
     case TC_BF16_3: return launch_form<false, 2, 3>(prm, cluster, grid, s);
     case TC_BF16_6: return launch_form<false, 3, 6>(prm, cluster, grid, s);

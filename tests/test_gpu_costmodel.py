@@ -5,9 +5,12 @@
 * Training (Adam, on the GPU) fits a smooth target and is bitwise reproducible.
 * Gain: trained on the autotuner's timings of two workloads, the model ranks the candidate
   tiles of a third workload; timing only its top 3 of 27 candidates must find a tile within
-  25 % of the exhaustive search's best (9x fewer timed candidates).
+  10 % of the exhaustive search's best, with 9x fewer timed candidates and less tuning
+  wall time.
 * Tuning never changes the arithmetic: tuned blocks still match the oracle.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -87,26 +90,31 @@ def test_model_ranking_gains_over_exhaustive_search(env):
         bb.bblock_set_option(ctx, "graphs", 0)
         bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B,
                           stream=stream)      # warm caches before timing
+        t0 = time.perf_counter()
         rep = bb.bblock_autotune(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B,
                                  stream=stream, repeats=3)
+        wall = time.perf_counter() - t0
         assert len(rep) == 27 and all(r["ms"] > 0 for r in rep)
-        data.append((ctx, inp, V, phis, B, rep))
+        data.append((ctx, inp, V, phis, B, rep, wall))
     X_train = np.concatenate([[r["features"] for r in d[5]] for d in data[:2]])
     y_train = np.log(np.concatenate([[r["ms"] for r in d[5]] for d in data[:2]]))
     cm = bb.CostModel(bb.bblock.TUNE_FEATURES, 32, seed=7)
     loss = cm.train(X_train, y_train, epochs=3000, lr=3e-3)
-    ctx, inp, V, phis, B, rep_ex = data[2]
+    ctx, inp, V, phis, B, rep_ex, wall_ex = data[2]
     best_ex = min(r["ms"] for r in rep_ex)
+    t0 = time.perf_counter()
     rep_m = bb.bblock_autotune(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B,
                                stream=stream, model=cm, top_k=3, repeats=3)
+    wall_m = time.perf_counter() - t0
     timed = [r for r in rep_m if r["ms"] > 0]
     best_m = min(r["ms"] for r in timed)
     default = [r["ms"] for r in rep_ex if (r["nc"], r["chunk"], r["slabs"]) == (48, 2, 0)]
-    print(f"train loss {loss:.4f}; exhaustive best {best_ex:.3f} ms over 27 timed; "
-          f"model top-3 best {best_m:.3f} ms over {len(timed)} timed; "
-          f"default tile {default[0] if default else float('nan'):.3f} ms")
-    assert len(timed) == 3
-    assert best_m <= 1.25 * best_ex
+    print(f"train loss {loss:.4f}; exhaustive best {best_ex:.3f} ms over 27 timed in "
+          f"{wall_ex:.2f} s; model top-3 best {best_m:.3f} ms over {len(timed)} timed in "
+          f"{wall_m:.2f} s; default tile {default[0] if default else float('nan'):.3f} ms")
+    assert len(timed) == 3 and len(timed) < len(rep_ex)
+    assert wall_m < wall_ex
+    assert best_m <= 1.10 * best_ex
     # the tuned context still computes the same blocks
     bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B, stream=stream)
     bb.bblock_status(ctx)

@@ -274,3 +274,13 @@ def test_l24_nev96_ndil32_sampled_entries(bb, torch_cuda, form):
                                     inp.momenta, inp.spins, inp.coeffs, d1s, d2s, d3s)
         sub = got[t][:, d1s][:, :, d2s][:, :, :, d3s]
         assert rel(sub, ref) <= TOL_FP64
+
+
+def test_fp64_probe_measures_both_paths(bb, torch_cuda):
+    """The FP64 throughput probe returns positive rates for DFMA and the FP64 MMA, within a
+    plausible range of a GPU's FP64 capability (0.05-20 TFLOP/s); the FP64 form's roofline
+    takes the DFMA rate as its peak."""
+    r = bb.bblock_probe_fp64(0)
+    print(f"FP64 probe: DFMA {r['dfma_tflops']:.3f} TFLOP/s, DMMA {r['dmma_tflops']:.3f} TFLOP/s")
+    for k in ("dfma_tflops", "dmma_tflops"):
+        assert 0.05 < r[k] < 20.0, r
