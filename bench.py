@@ -146,8 +146,16 @@ def projection_flops(X, n_ev, nd, n_alpha, n_beta, pairs):
 
 def folded_gemm_flops(X, nd, P, pairs):
     """Useful flops of the folded contraction run on the tensor cores: one complex GEMM
-    of M = d1 d2, N = P d3, K = 3 pairs X, 8 M N K (phase and colour sum folded in)."""
+    of M = d1 d2, N = P d3, K = 3 pairs X, 8 M N K (phase and colour sum folded in). With
+    the row-factored phase P is the number of distinct n0 of the momenta instead."""
     return 8.0 * nd[0] * nd[1] * (P * nd[2]) * (3 * pairs * X)
+
+
+def phase_columns(path, L, momenta):
+    """Phase columns per d3 of the tensor-core GEMM: every momentum, or (row-factored
+    path) the distinct x-components n0 mod L."""
+    mom = np.asarray(momenta).reshape(-1, 3)
+    return len({int(m[0]) % L for m in mom}) if path == "tc_rows" else len(mom)
 
 
 def contraction_df_inst(X, nd, P, pairs):
@@ -457,26 +465,33 @@ class Runner:
         return t_ms, prof, n_launch
 
 
-def tensor_roofline(form, prof, gemm_flops, alg_flops, steps, traffic, traffic_rec):
-    """The contraction's executed MMA flops (useful complex GEMM flops x piece products)
-    per launch over its average CUDA-event launch duration, against the pipe's peak."""
+def tensor_roofline(form, prof, gemm_flops, alg_flops, steps, traffic, traffic_rec, path):
+    """The contraction's algorithmic flops (the paper-ordering count of Eq. 1 per job: diquark,
+    colour singlet with the pair sum inside, momentum projection) per launch over its
+    average CUDA-event launch duration, against the pipe's measured peak. Beside it: the
+    complex GEMM the tensor cores run on this path (N = phase columns x d3) and the MMA
+    piece-product flops they execute for it."""
     nprod, peak = FORMS[form][2:4]
     nc, msc = prof.get("contract", (0, 0.0))
     if not nc:
         return None
     sec = msc / 1e3
+    alg = alg_flops * steps / sec / 1e12
     execd = gemm_flops * nprod * steps / sec / 1e12
-    return {"bound": "tensor", "kernel": "k_contract_tc", "achieved": execd, "peak": peak,
-            "unit": "TFLOP/s", "frac": execd / peak, "traffic": traffic,
+    return {"bound": "tensor", "kernel": "k_contract_tc", "path": path,
+            "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
+            "flops": "algorithmic: Eq. 1 in the paper's ordering, 42 Pi D1D2 X + (24 Pi + 8 P) "
+                     "D1D2D3 X per job (cmul 6, complex FMA 8)",
+            "flops_per_launch": alg_flops * steps / nc,
+            "traffic": traffic,
             "traffic_capture": traffic_rec.get("captured_workload") if traffic_rec else None,
             "peak_source": BF16_PEAK_SOURCE
                            + ("; TF32 = BF16 x 1.1/2.25 nominal" if form == "tf32x3" else ""),
-            "flops": "executed split-product MMA flops (useful complex GEMM flops x %d)" % nprod,
-            "useful_gemm_tflops": gemm_flops * steps / sec / 1e12,
-            "useful_frac": gemm_flops * steps / sec / 1e12 / peak,
-            "paper_ordering_tflops": alg_flops * steps / sec / 1e12,
-            "launches": nc, "avg_launch_ms": msc / nc,
-            "flops_per_launch": gemm_flops * nprod * steps / nc}
+            "gemm_tflops": gemm_flops * steps / sec / 1e12,
+            "gemm_frac": gemm_flops * steps / sec / 1e12 / peak,
+            "executed_tflops": execd, "executed_frac": execd / peak,
+            "executed": "MMA piece products: the path's complex GEMM x %d" % nprod,
+            "launches": nc, "avg_launch_ms": msc / nc}
 
 
 # The FP64 peak of the FP64 form's roofline: the DFMA rate bblock_probe_fp64 measures at the
@@ -537,7 +552,6 @@ def run_batched(args, R, w, rank, local, clk):
     blocks_per_step = len(job_nd) * P
     contract_alg = sum(contraction_flops(w.X, nd, P, pairs) for nd in job_nd)
     project_alg = sum(projection_flops(w.X, w.n_ev, nd, n_alpha, n_beta, pairs) for nd in job_nd)
-    gemm = sum(folded_gemm_flops(w.X, nd, P, pairs) for nd in job_nd)
     torch.cuda.synchronize(dev)
 
     def outputs(sel_t=None):
@@ -566,9 +580,12 @@ def run_batched(args, R, w, rank, local, clk):
     step = batch_step(ctx, outs)
     ms, prof, launches = R.measure(ctx, step, args.steps, args.warmup, sampler=clk)
     value = job_throughput(R.world, blocks_per_step, args.steps, ms / 1e3)
-    tkey = f"k_contract_tc/{head}/{w.name}"
+    path = bb.bblock_last_path(ctx)
+    ncols = phase_columns(path, w.L, inp.momenta)
+    gemm = sum(folded_gemm_flops(w.X, nd, ncols, pairs) for nd in job_nd)
+    tkey = f"k_contract_tc/{head}/{path}/{w.name}"
     traffic, trec = load_traffic(tkey)
-    roofline = tensor_roofline(head, prof, gemm, contract_alg, args.steps, traffic, trec)
+    roofline = tensor_roofline(head, prof, gemm, contract_alg, args.steps, traffic, trec, path)
 
     check = None
     if rank == 0 and not args.no_check:
@@ -589,16 +606,19 @@ def run_batched(args, R, w, rank, local, clk):
     if not args.no_forms:
         sub_t = list(range(min(8, n_t)))
         sub_nd = [inp.ndil[k] for k in range(w.n_noise) for _ in sub_t]
-        sub_gemm = sum(folded_gemm_flops(w.X, nd, P, pairs) for nd in sub_nd)
         sub_alg = sum(contraction_flops(w.X, nd, P, pairs) for nd in sub_nd)
         for name in dict.fromkeys([head, "bf16x6", "fp16x3", "tf32x3", "bf16x3"]):
             c2 = R.context(w, name, max_nd)
             o2 = outputs(len(sub_t))
             t_ms, pr, nl = R.measure(c2, batch_step(c2, o2, ts=sub_t), 2, 3)
             blocks = len(sub_nd) * P
+            pth = bb.bblock_last_path(c2)
+            sub_gemm = sum(folded_gemm_flops(w.X, nd, phase_columns(pth, w.L, inp.momenta), pairs)
+                           for nd in sub_nd)
             ent = {"blocks_per_s": job_throughput(R.world, blocks, 2, t_ms / 1e3),
                    "ms_per_step": t_ms / 2, "gpu_launches": nl,
-                   "tensor_roofline": tensor_roofline(name, pr, sub_gemm, sub_alg, 2, None, None),
+                   "tensor_roofline": tensor_roofline(name, pr, sub_gemm, sub_alg, 2, None, None,
+                                                      pth),
                    "kernels": kernel_table(pr, t_ms)}
             if rank == 0 and not args.no_check:
                 ent["oracle_check"] = oracle_check(
@@ -863,7 +883,6 @@ def run_single(args, R, w, rank, head, clk, steps, warmup, extras=True):
     blocks_per_step = n_t * P
     contract_alg = n_t * contraction_flops(w.X, nd, P, pairs)
     project_alg = n_t * projection_flops(w.X, w.n_ev, nd, n_alpha, n_beta, pairs)
-    gemm = n_t * folded_gemm_flops(w.X, nd, P, pairs)
     full_shape = args.n_t is None or not extras
 
     def measure(form, sampler=None, k=steps, wu=warmup):
@@ -878,6 +897,10 @@ def run_single(args, R, w, rank, head, clk, steps, warmup, extras=True):
 
     ctx, B, ms, prof, launches = measure(head, clk)
     value = job_throughput(R.world, blocks_per_step, steps, ms / 1e3)
+
+    def gemm_of(c):
+        return n_t * folded_gemm_flops(w.X, nd, phase_columns(bb.bblock_last_path(c), w.L,
+                                                              inp.momenta), pairs)
     if head == "fp64":
         traffic, trec = load_traffic(f"k_contract_fp64/fp64/{w.name}") if full_shape else (None, None)
         roofline = fp64_roofline(prof, contract_alg, steps, traffic, trec)
@@ -885,9 +908,11 @@ def run_single(args, R, w, rank, head, clk, steps, warmup, extras=True):
         roofline = df_roofline(prof, n_t * contraction_df_inst(w.X, nd, P, pairs), contract_alg,
                                steps)
     else:
-        traffic, trec = (load_traffic(f"k_contract_tc/{head}/{w.name}") if full_shape
+        path = bb.bblock_last_path(ctx)
+        traffic, trec = (load_traffic(f"k_contract_tc/{head}/{path}/{w.name}") if full_shape
                          else (None, None))
-        roofline = tensor_roofline(head, prof, gemm, contract_alg, steps, traffic, trec)
+        roofline = tensor_roofline(head, prof, gemm_of(ctx), contract_alg, steps, traffic, trec,
+                                   path)
 
     forms = {}
     if extras and not args.no_forms:
@@ -909,8 +934,8 @@ def run_single(args, R, w, rank, head, clk, steps, warmup, extras=True):
             elif name == "fp64":
                 ent["alu_roofline"] = fp64_roofline(pr, contract_alg, steps, None, None)
             else:
-                ent["tensor_roofline"] = tensor_roofline(name, pr, gemm, contract_alg, steps,
-                                                         None, None)
+                ent["tensor_roofline"] = tensor_roofline(name, pr, gemm_of(c2), contract_alg, steps,
+                                                         None, None, bb.bblock_last_path(c2))
             forms[name] = ent
             bb.bblock_destroy(c2)
 

@@ -181,6 +181,18 @@ size_t bblock_workspace_bytes(const bblock_ctx* ctx);
 /* Number of kernel launches enqueued by the last compute call. */
 int bblock_last_launch_count(const bblock_ctx* ctx);
 
+/* Contraction path of the last compute call (for reporting executed work; the blocks do
+ * not depend on it beyond rounding): the FP64 or double-float kernels; the tensor-core
+ * kernel with N tiles over (p, d3) columns, plain, as clusters sharing the diquark tile, or
+ * as CTA pairs sharing the third-quark tile; or the row-factored phase (N tiles over
+ * (distinct n0, d3), BBLOCK_OPT_TC_ROWS). -1 before any call or for a NULL context. */
+#define BBLOCK_PATH_FP64 0
+#define BBLOCK_PATH_TC 1
+#define BBLOCK_PATH_TC_CLUSTER 2
+#define BBLOCK_PATH_TC_PAIRS 3
+#define BBLOCK_PATH_TC_ROWS 4
+int bblock_last_path(const bblock_ctx* ctx);
+
 /* Number of waves the last compute call ran its jobs in: jobs are taken in list order, and
  * a wave holds as many as the workspace budget (BBLOCK_OPT_WAVE_MB) allows. 0 for a call
  * with no work or a NULL context. */
@@ -223,6 +235,18 @@ int bblock_last_wave_count(const bblock_ctx* ctx);
 #define BBLOCK_OPT_CORRUPT_CANARY 9  /* test hook (with BBLOCK_OPT_CHECKS): 1 makes the next
                                        call overwrite its first canary from the host, in
                                        stream order between the fill and the check, once */
+#define BBLOCK_OPT_TC_ROWS 13  /* FP16 form: the momentum phase factorised along the lattice,
+                                  e^{-i p.x} = w^{n0 x0} w^{n1 x1 + n2 x2} with w = e^{-2 pi i/L}:
+                                  the tensor cores sum each lattice row (fixed x1, x2) against
+                                  the third quark times w^{n0 x0} for each distinct n0 of the
+                                  momenta, and the row's sums are multiplied by
+                                  w^{n1 x1 + n2 x2} into one running sum per momentum. 0
+                                  (default): where it pays (at least twice as many momenta as
+                                  distinct n0) and the running sums fit TMEM; 1: wherever they
+                                  fit; 2: never (CTA pairs over all (p, d3) columns). With it,
+                                  BBLOCK_OPT_TC_NC sets the d3 columns per tile. Not with
+                                  index checks, per-momentum coefficients or the wait-limit
+                                  test hook */
 #define BBLOCK_OPT_TC_PROJECTION 12  /* mixed forms: 1 runs the projection (Eq. 2) on the
                                        tensor cores in the form's operand split, accumulated as
                                        in the contraction; 0 (default): FP32 FMA, which is

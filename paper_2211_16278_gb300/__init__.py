@@ -7,7 +7,7 @@ from .bblock import (BblockError, Context, CostModel, bblock_autotune,  # noqa: 
                      bblock_compute, bblock_compute_batch, bblock_compute_host,
                      bblock_contract_noalloc, bblock_create, bblock_destroy,
                      bblock_from_triplet, bblock_get_option, bblock_last_error,
-                     bblock_last_launch_count, bblock_last_wave_count,
+                     bblock_last_launch_count, bblock_last_path, bblock_last_wave_count,
                      bblock_mode_triplet, bblock_probe_fp64, bblock_profile_enable,
                      bblock_profile_read, bblock_set_option, bblock_status,
                      bblock_workspace_bytes, load)

@@ -33,7 +33,8 @@ PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16": 2, "df64": 3, "fp16x3": 4}
 EXPORTED = (
     "bblock_create", "bblock_destroy", "bblock_last_error", "bblock_status", "bblock_compute",
     "bblock_compute_host", "bblock_compute_batch", "bblock_workspace_bytes",
-    "bblock_last_launch_count", "bblock_last_wave_count", "bblock_profile_enable", "bblock_profile_read",
+    "bblock_last_launch_count", "bblock_last_wave_count", "bblock_last_path",
+    "bblock_profile_enable", "bblock_profile_read",
     "bblock_contract_noalloc", "bblock_set_option", "bblock_get_option", "bblock_autotune",
     "bblock_costmodel_create", "bblock_costmodel_destroy", "bblock_costmodel_num_params",
     "bblock_costmodel_get_params", "bblock_costmodel_set_params", "bblock_costmodel_gradient",
@@ -43,7 +44,7 @@ EXPORTED = (
 TUNE_FEATURES = 12
 OPTIONS = {"graphs": 1, "tc_nc": 2, "tc_chunk": 3, "slabs": 4, "checks": 5, "wave_mb": 6,
            "wait_limit_us": 7, "fail_next_alloc": 8, "corrupt_canary": 9, "tc_cluster": 10,
-           "host_chunks": 11, "tc_projection": 12}
+           "host_chunks": 11, "tc_projection": 12, "tc_rows": 13}
 
 
 class BblockError(RuntimeError):
@@ -112,6 +113,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.bblock_last_launch_count.restype = I
     lib.bblock_last_wave_count.argtypes = [P]
     lib.bblock_last_wave_count.restype = I
+    lib.bblock_last_path.argtypes = [P]
+    lib.bblock_last_path.restype = I
     lib.bblock_probe_fp64.argtypes = [I, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), P]
     lib.bblock_probe_fp64.restype = I
@@ -205,6 +208,14 @@ def bblock_last_launch_count(ctx: Context) -> int:
 
 def bblock_last_wave_count(ctx: Context) -> int:
     return int(load().bblock_last_wave_count(ctx.handle))
+
+
+PATHS = {0: "fp64", 1: "tc", 2: "tc_cluster", 3: "tc_pairs", 4: "tc_rows"}
+
+
+def bblock_last_path(ctx: Context) -> str:
+    """Contraction path of the last compute call (see BBLOCK_PATH_* in the header)."""
+    return PATHS.get(int(load().bblock_last_path(ctx.handle)), "none")
 
 
 def bblock_probe_fp64(device: int = 0, stream=None) -> dict:

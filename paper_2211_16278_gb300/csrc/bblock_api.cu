@@ -49,6 +49,8 @@ struct bblock_ctx {
   size_t tri_cap = 0;
   int last_launches = 0;
   int last_waves = 0;         // waves of jobs the last compute call ran in
+  int last_path = -1;         // contraction path of the last compute call (BBLOCK_PATH_*)
+  int graph_path = -1;
   size_t ws_budget = 0;
   // launch timing (bblock_profile_enable)
   bool prof = false;
@@ -85,6 +87,7 @@ struct bblock_ctx {
   int opt_tc_cluster = 0;     // tensor-core cluster size: 0 automatic, 1 none, 2 / 4 / 8
   int opt_host_chunks = 0;    // bblock_compute_host chunks of time slices (0: kHostChunks)
   int opt_tc_proj = 0;        // mixed forms: Eq. 2 on the tensor cores (1) or FP32 FMA (0)
+  int opt_tc_rows = 0;        // FP16 form: row-factored phase 0 where it pays, 1 where it fits, 2 never
   long long cycles_per_us = 2070;
 };
 
@@ -516,6 +519,60 @@ TcTiling choose_tc_tiling(const bblock_ctx* c, const std::vector<JobIn>& jobs, s
   return best;
 }
 
+// The row-factored phase of the FP16 form: e^{-i p.x} = w^{n0 x0} w^{n1 x1 + n2 x2}. The
+// contraction's N tile holds NC = nidx * nc columns (idx0, d3) for the nidx distinct n0 of
+// the momenta, and TMEM holds the chunk accumulators (4 NC columns) and a running sum per
+// momentum (2 nc each). It pays when the momenta are at least twice as many as their
+// distinct n0: the MMAs then cover nidx instead of P phase columns per d3.
+struct RfPlan {
+  bool on = false;
+  int nc = 16, nidx = 0, spr = 0;
+  int n0[kMaxRfIdx] = {};
+  int pidx0[kMaxRfP] = {}, pn1[kMaxRfP] = {}, pn2[kMaxRfP] = {};
+};
+
+RfPlan plan_rf(const bblock_ctx* c, int n_mom, int per_mom, int form, int n_pairs, int G,
+               int nc_opt) {
+  RfPlan r;
+  if (form != TC_F16_3 || per_mom || c->opt_checks || c->opt_wait_us || c->opt_tc_rows == 2 ||
+      n_mom < 1 || n_mom > kMaxRfP || c->phase_mom.size() != (size_t)3 * n_mom)
+    return r;
+  const int L = c->cfg.L;
+  auto md = [L](int v) { const int m = v % L; return m < 0 ? m + L : m; };
+  for (int p = 0; p < n_mom; ++p) {
+    const int n0 = md(c->phase_mom[3 * p]);
+    int idx = -1;
+    for (int k = 0; k < r.nidx; ++k)
+      if (r.n0[k] == n0) idx = k;
+    if (idx < 0) {
+      if (r.nidx == kMaxRfIdx) return RfPlan{};
+      idx = r.nidx;
+      r.n0[r.nidx++] = n0;
+    }
+    r.pidx0[p] = idx;
+    r.pn1[p] = md(c->phase_mom[3 * p + 1]);
+    r.pn2[p] = md(c->phase_mom[3 * p + 2]);
+  }
+  if (c->opt_tc_rows == 0 && n_mom < 2 * r.nidx) return RfPlan{};
+  auto fits = [&](int nc) {
+    // B rows (idx0, d3) are built by the plain kernel's third-quark producers: <= 48
+    return nc >= 16 && nc % 16 == 0 && r.nidx * nc <= tc_max_nc(form, false) &&
+           4 * r.nidx * nc + 2 * n_mom * nc <= 512;
+  };
+  if (nc_opt > 0) {
+    if (!fits(nc_opt)) return RfPlan{};
+    r.nc = nc_opt;
+  } else {
+    r.nc = 0;
+    for (int nc = 48; nc >= 16 && !r.nc; nc -= 16)
+      if (fits(nc)) r.nc = nc;
+    if (!r.nc) return RfPlan{};
+  }
+  r.spr = (L * n_pairs + G - 1) / G;
+  r.on = true;
+  return r;
+}
+
 // Tensor-core forms: FP32 projection, tcgen05 contraction, FP64 slab reduction.
 int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& sp, int n_mom,
                 int per_mom, cudaStream_t s) {
@@ -532,6 +589,12 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
   const int min_slabs = (int)std::min<long long>(
       X, ((long long)X * sp.n_pairs + max_groups_per_unit - 1) / max_groups_per_unit);
   const int max_slabs = std::max(64, min_slabs);
+  // the row-factored phase (FP16 form): slabs are ranges of lattice rows, each unit drains
+  // at most 256 times
+  const int L = c->cfg.L, n_rows = L * L;
+  const RfPlan rp = plan_rf(c, n_mom, per_mom, form, sp.n_pairs, G, c->opt_tc_nc);
+  const int rf_cpr = rp.on ? (rp.spr + chunk_stages - 1) / chunk_stages : 1;
+  const int rf_min_slabs = rp.on ? (n_rows + std::max(1, 256 / rf_cpr) - 1) / std::max(1, 256 / rf_cpr) : 1;
   // checks option: a canary after the converted inputs and every field and partial block
   const size_t canary_bytes = c->opt_checks ? (size_t)(sp.n1 + sp.n2 + n3_fields + 2) * kCanaryBytes : 0;
   // FP32 copies of a job's inputs (V and the three phi_i), converted once per call
@@ -556,7 +619,12 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     }
     ++c->last_waves;
     const int nj = (int)(end - job_idx);
-    const TcTiling tt = choose_tc_tiling(c, jobs, job_idx, end, P_launch, form, c->opt_tc_nc);
+    TcTiling tt = choose_tc_tiling(c, jobs, job_idx, end, P_launch, form, c->opt_tc_nc);
+    if (rp.on) {   // row-factored: plain CTAs, B rows (idx0, d3)
+      tt.cluster = 1;
+      tt.share_b = false;
+      tt.nc = rp.nidx * rp.nc;
+    }
     const int NC = tt.nc, CL = tt.cluster;
     if (NC > tc_max_nc(form, tt.share_b))
       return fail(c, BBLOCK_ERR_INVALID_ARG, "N tile of %d columns exceeds this form's %d", NC,
@@ -568,18 +636,32 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       return tt.share_b ? (mt + 1) / 2 : mt;
     };
     const int n_group = tt.share_b ? NC : CL * NC;
+    // N tiles of a job: groups of (p, d3) columns, or (row-factored) of d3 columns
+    auto unit_n_tiles = [&](const JobIn& j) -> long long {
+      if (rp.on) return (j.nd[2] + rp.nc - 1) / rp.nc;
+      return ((long long)P_launch * j.nd[2] + n_group - 1) / n_group;
+    };
     long long tiles = 0, max_elems = 0;
     int max_ndf = 0;
     for (size_t k = job_idx; k < end; ++k) {
       const JobIn& j = jobs[k];
-      tiles += unit_m_tiles(j) * ((P_launch * j.nd[2] + (long long)n_group - 1) / n_group);
+      tiles += unit_m_tiles(j) * unit_n_tiles(j);
       for (int i = 0; i < 3; ++i) max_ndf = std::max(max_ndf, j.nd[i]);
       max_elems = std::max(max_elems, (long long)P_launch * j.nd[0] * j.nd[1] * j.nd[2]);
     }
-    int n_slab = c->opt_slabs > 0 ? std::max(min_slabs, std::min(c->opt_slabs, X))
-                                   : std::max(min_slabs, choose_slabs(tiles, grid_cap / CL, X, 1, max_slabs));
-    int sites_per_slab = (X + n_slab - 1) / n_slab;
-    n_slab = (X + sites_per_slab - 1) / sites_per_slab;
+    int n_slab, sites_per_slab, rows_per_slab = 0;
+    if (rp.on) {
+      n_slab = c->opt_slabs > 0 ? std::max(rf_min_slabs, std::min(c->opt_slabs, n_rows))
+                                : std::max(rf_min_slabs, choose_slabs(tiles, grid_cap, n_rows, 1, max_slabs));
+      rows_per_slab = (n_rows + n_slab - 1) / n_slab;
+      n_slab = (n_rows + rows_per_slab - 1) / rows_per_slab;
+      sites_per_slab = rows_per_slab * L;
+    } else {
+      n_slab = c->opt_slabs > 0 ? std::max(min_slabs, std::min(c->opt_slabs, X))
+                                : std::max(min_slabs, choose_slabs(tiles, grid_cap / CL, X, 1, max_slabs));
+      sites_per_slab = (X + n_slab - 1) / n_slab;
+      n_slab = (X + sites_per_slab - 1) / sites_per_slab;
+    }
     // FP16 form: three per-line maxima per job (the operand scales), at the wave's start
     const bool amax_on = tc_form_needs_amax(form);
     const size_t amax_bytes = amax_on ? align_up((size_t)3 * nj * sizeof(uint32_t), 256) : 0;
@@ -662,7 +744,7 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
       ws = base;
       const int m_tiles = (int)unit_m_tiles(j);                       // (d1, d2) pairs
       // groups of CL N tiles of NC (p, d3) columns: a cluster unit covers one group
-      const int n_tiles = (P_launch * j.nd[2] + n_group - 1) / n_group;
+      const int n_tiles = (int)unit_n_tiles(j);
       for (int set = 0; set < sp.n_coef_sets; ++set) {
         TcJob& tj = tjobs[set][k];
         for (int i = 0; i < 4; ++i) { tj.q1[i] = q1[i]; tj.q2[i] = q2[i]; }
@@ -697,7 +779,15 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     const size_t jbytes = align_up((size_t)nj * sizeof(TcJob), 256);
     const size_t sofs = fbytes + jbytes * sp.n_coef_sets;
     const size_t cofs = sofs + align_up(segs.size() * sizeof(F32ConvSeg), 256);
-    std::vector<char> tab(cofs + canaries.size() * sizeof(uint32_t*));
+    // row-factored: w^k = e^{-2 pi i k / L}, k = 0..L-1, in FP64 rounded to FP32
+    const size_t wofs = align_up(cofs + canaries.size() * sizeof(uint32_t*), 256);
+    std::vector<char> tab(wofs + (rp.on ? (size_t)L * sizeof(float2) : 0));
+    if (rp.on) {
+      float2* om = reinterpret_cast<float2*>(tab.data() + wofs);
+      const double two_pi = 6.283185307179586476925286766559;
+      for (int k = 0; k < L; ++k)
+        om[k] = make_float2((float)std::cos(two_pi * k / L), (float)-std::sin(two_pi * k / L));
+    }
     memcpy(tab.data(), fields.data(), fields.size() * sizeof(ProjFieldF));
     for (int set = 0; set < sp.n_coef_sets; ++set)
       memcpy(tab.data() + fbytes + jbytes * set, tjobs[set].data(), (size_t)nj * sizeof(TcJob));
@@ -765,6 +855,24 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     prm.NC = NC;
     prm.share_b = tt.share_b ? 1 : 0;
     prm.chunk_stages = chunk_stages;
+    c->last_path = rp.on ? BBLOCK_PATH_TC_ROWS
+                         : tt.share_b ? BBLOCK_PATH_TC_PAIRS
+                                      : CL > 1 ? BBLOCK_PATH_TC_CLUSTER : BBLOCK_PATH_TC;
+    if (rp.on) {
+      prm.rf = 1;
+      prm.L = L;
+      prm.rf_spr = rp.spr;
+      prm.rf_rows_per_slab = rows_per_slab;
+      prm.rf_nc = rp.nc;
+      prm.rf_nidx = rp.nidx;
+      for (int k = 0; k < rp.nidx; ++k) prm.rf_n0[k] = rp.n0[k];
+      for (int p = 0; p < n_mom; ++p) {
+        prm.rf_pidx0[p] = rp.pidx0[p];
+        prm.rf_pn1[p] = rp.pn1[p];
+        prm.rf_pn2[p] = rp.pn2[p];
+      }
+      prm.rf_omega = reinterpret_cast<const float2*>(c->d_tab + wofs);
+    }
     prm.status = c->d_status;
     prm.checks = c->opt_checks;
     prm.dbg = c->d_dbg;
@@ -798,6 +906,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
              cudaStream_t s) {
   c->last_launches = 0;
   c->last_waves = 0;
+  c->last_path = fp64_like(c->cfg) ? BBLOCK_PATH_FP64 : -1;
   c->last_stream = s;
   c->call_tab_bytes = 0;
   if (jobs.empty() || n_mom == 0) return BBLOCK_OK;
@@ -1069,7 +1178,8 @@ std::vector<uint64_t> call_signature(const bblock_ctx* c, const std::vector<JobI
               ((uint64_t)c->opt_tc_chunk << 32) | ((uint64_t)c->opt_slabs << 40));
   k.push_back((uint64_t)n_mom | ((uint64_t)n_spin << 32));
   k.push_back((uint64_t)wave_budget(c) ^ ((uint64_t)c->opt_tc_cluster << 60) ^
-              ((uint64_t)c->opt_tc_proj << 56) ^ ((uint64_t)c->prof << 52));
+              ((uint64_t)c->opt_tc_proj << 56) ^ ((uint64_t)c->prof << 52) ^
+              ((uint64_t)c->opt_tc_rows << 48));
   for (int i = 0; i < 3 * n_mom; ++i) k.push_back((uint64_t)(uint32_t)momenta[i]);
   for (int i = 0; i < 3 * n_spin; ++i) k.push_back((uint64_t)(uint32_t)spin_idx[i]);
   const int n_coef = 2 * n_spin * (per_mom ? n_mom : 1);
@@ -1109,6 +1219,7 @@ int run_jobs_cached(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t
     c->graph_pending = !c->graph_timed.empty();
     c->last_launches = c->graph_launches;
     c->last_waves = c->graph_waves;
+    c->last_path = c->graph_path;
     c->last_stream = s;
     return BBLOCK_OK;
   }
@@ -1163,6 +1274,7 @@ int run_jobs_cached(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t
   c->graph_sig = sig;
   c->graph_launches = c->last_launches;
   c->graph_waves = c->last_waves;
+  c->graph_path = c->last_path;
   CK(c, cudaGraphLaunch(exec, s));
   c->graph_pending = !c->graph_timed.empty();
   c->last_stream = s;
@@ -1205,6 +1317,22 @@ CallPlan plan_call(const bblock_ctx* c, int n_t, const int nd[3], int n_mom, int
   const int max_slabs = std::max(64, min_slabs);
   std::vector<JobIn> one(1);
   one[0].nd[0] = nd[0]; one[0].nd[1] = nd[1]; one[0].nd[2] = nd[2];
+  const RfPlan rp = plan_rf(c, n_mom, 0, tc_form_of(c->cfg), pairs, G, nc_opt);
+  if (rp.on) {   // row-factored: units over d3 tiles and slabs of lattice rows
+    const int L = c->cfg.L, n_rows = L * L;
+    const int cpr = (rp.spr + pl.chunk - 1) / pl.chunk;
+    const int min_s = (n_rows + std::max(1, 256 / cpr) - 1) / std::max(1, 256 / cpr);
+    pl.nc = rp.nidx * rp.nc;
+    const long long n_tiles = (nd[2] + rp.nc - 1) / rp.nc;
+    const long long tiles = (long long)n_t * (((long long)nd[0] * nd[1] + 127) / 128) * n_tiles;
+    int ns = slabs_opt > 0 ? std::max(min_s, std::min(slabs_opt, n_rows))
+                           : std::max(min_s, choose_slabs(tiles, c->num_sms, n_rows, 1, max_slabs));
+    const int rps = (n_rows + ns - 1) / ns;
+    pl.n_slab = (n_rows + rps - 1) / rps;
+    pl.units = tiles * pl.n_slab;
+    pl.pad = (double)(n_tiles * rp.nc) / nd[2] - 1.0;
+    return pl;
+  }
   // the tiling run_jobs_tc would pick with this candidate's N tile
   const TcTiling tt = choose_tc_tiling(c, one, 0, 1, n_mom, tc_form_of(c->cfg), nc_opt);
   pl.nc = tt.nc;
@@ -1653,6 +1781,7 @@ size_t bblock_workspace_bytes(const bblock_ctx* c) {
 
 int bblock_last_launch_count(const bblock_ctx* c) { return c ? c->last_launches : 0; }
 int bblock_last_wave_count(const bblock_ctx* c) { return c ? c->last_waves : 0; }
+int bblock_last_path(const bblock_ctx* c) { return c ? c->last_path : -1; }
 
 int bblock_autotune(bblock_ctx* c, int n_t, const void* V, const void* phi1, const void* phi2,
                     const void* phi3, int nd1, int nd2, int nd3, const int32_t* momenta,
@@ -1813,6 +1942,11 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) break;
       c->opt_tc_cluster = value;
       return BBLOCK_OK;
+    case BBLOCK_OPT_TC_ROWS:
+      if (value < 0 || value > 2) break;
+      c->opt_tc_rows = value;
+      drop_graph(c);
+      return BBLOCK_OK;
     case BBLOCK_OPT_TC_PROJECTION:
       if (value != 0 && value != 1) break;
       c->opt_tc_proj = value;
@@ -1847,6 +1981,7 @@ int bblock_get_option(const bblock_ctx* c, int option) {
     case BBLOCK_OPT_TC_CLUSTER: return c->opt_tc_cluster;
     case BBLOCK_OPT_HOST_CHUNKS: return c->opt_host_chunks;
     case BBLOCK_OPT_TC_PROJECTION: return c->opt_tc_proj;
+    case BBLOCK_OPT_TC_ROWS: return c->opt_tc_rows;
     case BBLOCK_OPT_CHECKS: return c->opt_checks;
     default: return BBLOCK_ERR_INVALID_ARG;
   }

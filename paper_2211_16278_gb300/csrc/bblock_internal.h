@@ -8,6 +8,9 @@ namespace bb {
 
 constexpr int kMaxTerms = 4;    // distinct gamma spins folded into one line-3 field
 constexpr int kMaxPairs = 16;   // distinct (alpha, beta) spin pairs
+// Row-factored tensor-core contraction: momenta per launch and distinct n0 values.
+constexpr int kMaxRfP = 16;
+constexpr int kMaxRfIdx = 8;
 // Momenta handled by one contraction launch of the FP64 form (10) and of the double-float
 // form (8): the largest counts whose accumulators fit the registers without spills.
 constexpr int kMaxPGroup = 10;
@@ -125,6 +128,22 @@ struct TcParams {
   // CTA pairs (FP16 form, cluster = 2): the two CTAs of a cluster share the third-quark tile
   // of one N tile and take adjacent M tiles; a job's m_tiles then counts pairs of M tiles
   int share_b;
+  // Row-factored phase (FP16 form): e^{-i p.x} = w^{n0 x0} w^{n1 x1 + n2 x2}, w = e^{-2 pi i/L}.
+  // The MMA sums one lattice row (x1, x2 fixed, x0 = 0..L-1) against the third quark times
+  // w^{n0 x0} for each distinct n0 of the momenta (B rows (idx0, d3), NC = rf_nidx * rf_nc);
+  // the epilogue multiplies each row's sums by w^{n1 x1 + n2 x2} into one FP32 running sum
+  // per momentum. A unit's slab is a range of rows [x_begin, x_end) of the L^2 rows; a row
+  // takes rf_spr stages of groups (x0, pair), the last one padded.
+  int rf;                        // 1: the row-factored FP16 contraction (launch_contract_tc)
+  int L;
+  int rf_spr;
+  int rf_rows_per_slab;
+  int rf_nc;                     // d3 columns per N tile
+  int rf_nidx;                   // distinct n0 (mod L) of the momenta
+  int rf_n0[kMaxRfIdx];          // those n0, reduced to [0, L)
+  int rf_pidx0[kMaxRfP];         // momentum p: index of its n0
+  int rf_pn1[kMaxRfP], rf_pn2[kMaxRfP];   // momentum p: n1, n2 reduced to [0, L)
+  const float2* rf_omega;        // w^k, k = 0..L-1, FP64 rounded to FP32
   int* status;
   // index checks (debug option): every global access is checked against its buffer; the
   // first violation is recorded in dbg[0..3] = (site code, job, index, bound) and skipped

@@ -407,6 +407,23 @@ __device__ __forceinline__ Unit decode_unit(const TcParams& prm, long long u, in
   return w;
 }
 
+// Row-factored units: (job, 128-pair tile, N tile, slab of lattice rows); x_begin / x_end
+// are rows, and every row takes rf_spr stages.
+__device__ __forceinline__ Unit decode_unit_rf(const TcParams& prm, long long u) {
+  Unit w;
+  w.job = tc_find_job(prm.jobs, prm.n_jobs, u);
+  const TcJob& J = prm.jobs[w.job];
+  long long r = u - J.unit_begin;
+  w.mt = (int)(r % J.m_tiles);
+  r /= J.m_tiles;
+  w.nt = (int)(r % J.n_tiles);
+  w.slab = (int)(r / J.n_tiles);
+  w.x_begin = w.slab * prm.rf_rows_per_slab;
+  w.x_end = min(prm.L * prm.L, w.x_begin + prm.rf_rows_per_slab);
+  w.n_stages = (w.x_end - w.x_begin) * prm.rf_spr;
+  return w;
+}
+
 // Projection units: (128-row tile, field, N tile), the row tile outermost so that the CTAs
 // running at once share their V tiles in L2; the K sum (eigenvector index l) runs over
 // ceil(N_ev / KS) stages. N tiles past the field's columns are empty.
@@ -455,10 +472,17 @@ __device__ __forceinline__ bool wait_bounded(uint32_t mbar, uint32_t parity,
 // shared::cta -> shared::cluster copies counted on the peer's stage barrier). Each CTA
 // then runs its own MMAs on its diquark rows and the whole third-quark tile, which can be
 // up to 80 complex columns wide because the accumulators are single-buffered there.
+//
+// RF (C = 1, the FP16 form): the row-factored phase. A chunk of MMAs never crosses a lattice
+// row; the B rows are (idx0, d3) with the factor w^{n0 x0} of the idx0-th distinct n0; the
+// epilogue adds each drained chunk, times the row's w^{n1 x1 + n2 x2}, into the running sum
+// of every momentum with that n0. The stages hold two stage buffers (the wide layout) and
+// the w table follows them in shared memory.
 template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C, bool PROJ, bool F16 = false,
-          bool SHB = false>
+          bool SHB = false, bool RF = false>
 __device__ __forceinline__ void tc_body(const TcParams& prm) {
   using R = Roles<TF32, SHB ? 1 : C>;
+  static_assert(!RF || (F16 && C == 1 && !CHECKS && !PROJ), "row-factored: FP16, plain CTAs");
   static_assert(!PROJ || (C == 1 && !CHECKS), "the projection runs without clusters or checks");
   static_assert(!F16 || (!TF32 && LEVELS == 2 && (C == 1 || SHB) && !PROJ),
                 "the FP16 form: two pieces, contraction only, clusters only as CTA pairs");
@@ -467,7 +491,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   constexpr int G = TF32 ? 8 : 16;                 // (site, pair) groups per stage
   // transaction bytes a stage receives from the peers: their diquark rows, every plane
   constexpr uint32_t kPeerTx = (uint32_t)((C - 1) * (R::kARows / 8) * 768 * LEVELS * 2);
-  using Lay = TcLayout<TF32, LEVELS, F16, SHB>;
+  using Lay = TcLayout<TF32, LEVELS, F16, SHB || RF>;
   constexpr int STAGES = Lay::kStages;
   constexpr int STAGE_BYTES = Lay::kStageBytes;
   constexpr bool kTwoMma = Lay::kTwoMma;   // complex product as two N = 2 NC MMAs
@@ -477,6 +501,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   constexpr int kLoadRun = (!kShareA && !CHECKS) ? 8 : 4;
   auto decode = [&](long long u) -> Unit {
     if constexpr (PROJ) return decode_unit_proj(prm, u, 3 * G);
+    else if constexpr (RF) return decode_unit_rf(prm, u);
     else return decode_unit(prm, u, G);
   };
   // piece products (i, j): leading (0, 0) first, then by increasing i + j
@@ -498,7 +523,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   const int np = prm.n_pairs;
   // accumulator buffers: double-buffered [lead | corr] (4 NC columns each) and the FP32
   // running sum (2 NC) while 10 NC <= 512 TMEM columns; single-buffered beyond
-  const int nbuf = 10 * NC <= kTmemCols ? 2 : 1;
+  const int nbuf = (!RF && 10 * NC <= kTmemCols) ? 2 : 1;
   // CTA pairs: transaction bytes of the peer's third-quark rows (NC / 2 rows, every plane)
   const uint32_t peer_tx = SHB ? (uint32_t)((NC / 16) * LEVELS * Lay::kBPlanes * 768) : kPeerTx;
 
@@ -514,6 +539,11 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
     mbar_init(smem_u32(&bar_final), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // row-factored: the w^k table after the stage buffers
+  float2* s_omega = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);
+  if constexpr (RF) {
+    for (int k = tid; k < prm.L; k += blockDim.x) s_omega[k] = prm.rf_omega[k];
   }
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -620,6 +650,12 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
           row_ok = m < nd1 * nd2;
           const int d1 = row_ok ? m / nd2 : 0, d2 = row_ok ? m - d1 * nd2 : 0;
           off1 = d1; off2 = d2; s1 = nd1; s2 = nd2;
+        } else if constexpr (RF) {
+          // N side: w^{n0 x0} x third quark of the row (idx0, d3); pidx holds n0 (mod L)
+          const int idx0 = rr / prm.rf_nc;
+          const int d3 = w.nt * prm.rf_nc + (rr - idx0 * prm.rf_nc);
+          row_ok = row_used && d3 < nd3 && idx0 < prm.rf_nidx;
+          off1 = row_ok ? d3 : 0; s1 = nd3; pidx = row_ok ? prm.rf_n0[idx0] : 0;
         } else {
           // N side: phase x third quark of the column n = p * nd3 + d3
           const int n = (kShareA ? w.nt * C + (int)rank : w.nt) * NC + rr;
@@ -640,7 +676,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
         }
         __syncwarp();
         named_bar(kBarProd, R::kProdThreads);
-        phase_p = prm.phase + (size_t)pidx * prm.X;
+        if constexpr (!RF) phase_p = prm.phase + (size_t)pidx * prm.X;
       }
       for (int st = 0; st < w.n_stages; ++st, ++s_g) {
         const int slot = (int)(s_g % STAGES);
@@ -690,8 +726,14 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                 }
             }
           } else {
-            // first group of this thread's run of NG
-            const int gi0 = st * G + g0;
+            // the stage's sites [sx0, sx1) and this thread's first group of its run of NG
+            // (row-factored: the stage's row, groups counted from the row's first site)
+            int sx0 = w.x_begin, sx1 = w.x_end, gi0 = st * G + g0;
+            if constexpr (RF) {
+              sx0 = (w.x_begin + st / prm.rf_spr) * prm.L;
+              sx1 = sx0 + prm.L;
+              gi0 = (st % prm.rf_spr) * G + g0;
+            }
             int xl = gi0 / np, pr = gi0 - xl * np;
             uint32_t vmask = 0;   // groups of this run that lie inside the slab and a used row
 #pragma unroll
@@ -703,9 +745,9 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
 #pragma unroll
               for (int j = 0; j < kLoadRun; ++j) {
                 if (half * kLoadRun + j >= NG) break;
-                const int x = w.x_begin + xl;
-                vld[j] = row_ok && x < w.x_end;
-                int xs = vld[j] ? x : w.x_begin;
+                const int x = sx0 + xl;
+                vld[j] = row_ok && x < sx1;
+                int xs = vld[j] ? x : sx0;
                 if (CHECKS) {
                   const long long fl = 3LL * prm.X * s1;            // elements of a field
                   bool good = idx_ok(prm, (long long)xs * 3 * s1 + off1 + 2LL * s1, fl, is_a ? 1 : 3, w.job) &&
@@ -722,7 +764,8 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                 } else {
                   const float2* q = s_q3[pr] + (size_t)xs * 3 * s1 + off1;
                   ld[j][0] = q[0]; ld[j][1] = q[s1]; ld[j][2] = q[2 * s1];
-                  ld[j][3] = phase_p[xs];
+                  if constexpr (RF) ld[j][3] = s_omega[(pidx * (xs - sx0)) % prm.L];
+                  else ld[j][3] = phase_p[xs];
                 }
                 if (++pr == np) { pr = 0; ++xl; }
               }
@@ -866,12 +909,15 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
       bool stop = false;
       for (long long u = u0; u < prm.total_units && !stop; u += du) {
         const Unit w = decode(u);
+        // chunks of chunk_stages stages; row-factored: no chunk crosses a lattice row
+        const int spr = RF ? prm.rf_spr : w.n_stages;
         for (int st = 0; st < w.n_stages; ++st, ++s_g) {
           const int slot = (int)(s_g % STAGES);
           const int buf = (int)(c_g % nbuf);
-          const bool chunk_first = (st % prm.chunk_stages) == 0;
-          const bool chunk_last = (st % prm.chunk_stages) == prm.chunk_stages - 1 ||
-                                  st == w.n_stages - 1;
+          const int sr = st % spr;
+          const bool chunk_first = (sr % prm.chunk_stages) == 0;
+          const bool chunk_last = (sr % prm.chunk_stages) == prm.chunk_stages - 1 ||
+                                  sr == spr - 1;
           // the chunk's accumulator buffer must have been drained (its previous use)
           if (chunk_first && c_g >= nbuf) {
             if (!wait_bounded(smem_u32(&bar_acc_empty[buf]), (uint32_t)(((c_g / nbuf) + 1) & 1),
@@ -944,7 +990,9 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
     long long c_g = 0;
     for (long long u = u0; u < prm.total_units; u += du) {
       const Unit w = decode(u);
-      const int n_chunks = (w.n_stages + prm.chunk_stages - 1) / prm.chunk_stages;
+      const int spr = RF ? prm.rf_spr : w.n_stages;            // stages per chunk row
+      const int cpr = (spr + prm.chunk_stages - 1) / prm.chunk_stages;
+      const int n_chunks = (spr > 0 ? w.n_stages / spr : 0) * cpr;
       for (int ch = 0; ch < n_chunks; ++ch, ++c_g) {
         const int buf = (int)(c_g % nbuf);
         bool ok = !abort_flag;
@@ -953,7 +1001,47 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                             &abort_flag, prm.status, prm.wait_limit);
         // the TMEM loads below are warp-collective: decide per warp
         ok = __all_sync(0xffffffffu, ok);
-        if (ok) {
+        if (ok && RF) {
+          // row-factored: chunk sums t = lead + corr of each n0 block, times the row's
+          // w^{n1 x1 + n2 x2}, into the running sum of every momentum with that n0
+          tc_fence_after();
+          const uint32_t lead = tmem + lane_base;
+          const int row = w.x_begin + ch / cpr;
+          const int x1 = row % prm.L, x2 = row / prm.L;
+          const int ncol = prm.rf_nc;
+          for (int i0 = 0; i0 < prm.rf_nidx; ++i0) {
+            for (int col = 0; col < ncol; col += 16) {
+              float tr[16], ti[16], cr[16], ci[16];
+              tmem_ld16(lead + i0 * ncol + col, tr);
+              tmem_ld16(lead + NC + i0 * ncol + col, ti);
+              tmem_ld16(lead + 2 * NC + i0 * ncol + col, cr);
+              tmem_ld16(lead + 3 * NC + i0 * ncol + col, ci);
+              tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 16; ++i) { tr[i] += cr[i]; ti[i] += ci[i]; }
+              for (int p = 0; p < prm.P; ++p) {
+                if (prm.rf_pidx0[p] != i0) continue;
+                const float2 ph = s_omega[(prm.rf_pn1[p] * x1 + prm.rf_pn2[p] * x2) % prm.L];
+                const uint32_t rp = run_r + (uint32_t)(p * 2 * ncol + col);
+                float rr[16], ri[16];
+                if (ch > 0) {
+                  tmem_ld16(rp, rr);
+                  tmem_ld16(rp + ncol, ri);
+                  tmem_wait_ld();
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                  const float a = ch > 0 ? rr[i] : 0.f, b = ch > 0 ? ri[i] : 0.f;
+                  rr[i] = fmaf(ph.x, tr[i], fmaf(-ph.y, ti[i], a));
+                  ri[i] = fmaf(ph.x, ti[i], fmaf(ph.y, tr[i], b));
+                }
+                tmem_st16(rp, rr);
+                tmem_st16(rp + ncol, ri);
+              }
+            }
+          }
+          tmem_wait_st();
+        } else if (ok) {
           tc_fence_after();
           const uint32_t lead = tmem + lane_base + (uint32_t)(buf * 4 * NC);
           for (int col = 0; col < 2 * NC; col += 16) {
@@ -991,6 +1079,29 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
               }
             }
           }
+        } else if (RF && ok && ch == n_chunks - 1) {
+          // unit done (row-factored): every momentum's running sum is its partial block
+          const TcJob& J = prm.jobs[w.job];
+          const int m = w.mt * kTcM + row;
+          const int M = J.nd1 * J.nd2, nd3 = J.nd3, ncol = prm.rf_nc;
+          for (int p = 0; p < prm.P; ++p)
+            for (int col = 0; col < ncol; col += 16) {
+              float vr[16], vi[16];
+              __syncwarp();
+              const uint32_t rp = run_r + (uint32_t)(p * 2 * ncol + col);
+              tmem_ld16(rp, vr);
+              tmem_ld16(rp + ncol, vi);
+              tmem_wait_ld();
+              if (m < M) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                  const int d3 = w.nt * ncol + col + i;
+                  if (d3 < nd3)
+                    J.partial[(((size_t)w.slab * prm.P + p) * M + m) * nd3 + d3] =
+                        make_float2(vr[i], vi[i]);
+                }
+              }
+            }
         } else if (!PROJ && ok && ch == n_chunks - 1) {
           // unit done: write the FP32 running sum as this slab's partial block
           const TcJob& J = prm.jobs[w.job];
@@ -1038,6 +1149,12 @@ __global__ void __launch_bounds__(Roles<TF32, C>::kThreads, 1)
 k_contract_tc(const __grid_constant__ TcParams prm) {
   tc_body<TF32, LEVELS, NPROD, CHECKS, C, false, F16>(prm);
 }
+// The FP16 form with the row-factored momentum phase.
+__global__ void __launch_bounds__(Roles<false, 1>::kThreads, 1)
+k_contract_tc_rows(const __grid_constant__ TcParams prm) {
+  tc_body<false, 2, 3, false, 1, false, true, false, true>(prm);
+}
+
 // The FP16 form as CTA pairs that share the third-quark tile (clusters of 2).
 __global__ void __launch_bounds__(Roles<false, 1>::kThreads, 1)
 k_contract_tc_pair(const __grid_constant__ TcParams prm) {
@@ -1127,9 +1244,29 @@ cudaError_t launch_pair(const TcParams& prm, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The row-factored FP16 contraction: one CTA per SM; the stages, then the w^k table.
+cudaError_t launch_rows(const TcParams& prm, int grid, cudaStream_t s) {
+  using Lay = TcLayout<false, 2, true, true>;
+  const size_t smem = (size_t)Lay::kStages * Lay::kStageBytes + 128 * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_contract_tc_rows,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_contract_tc_rows<<<grid, Roles<false, 1>::kThreads, smem, s>>>(prm);
+  return cudaGetLastError();
+}
+
 // The FP16 form: two pieces, three products; plain CTAs (with or without index checks), or
-// CTA pairs sharing the third-quark tile (cluster = 2, unchecked).
+// CTA pairs sharing the third-quark tile (cluster = 2, unchecked), or the row-factored
+// phase (unchecked).
 cudaError_t launch_form_f16(const TcParams& prm, int cluster, int grid, cudaStream_t s) {
+  if (prm.rf) {
+    if (prm.checks || cluster != 1 || prm.share_b || prm.L < 1 || prm.L > 128 ||
+        prm.rf_nidx < 1 || prm.rf_nidx > kMaxRfIdx || prm.P > kMaxRfP || prm.rf_spr < 1 ||
+        prm.rf_nc < 16 || prm.rf_nc % 16 != 0 || prm.NC != prm.rf_nidx * prm.rf_nc ||
+        4 * prm.NC + 2 * prm.P * prm.rf_nc > kTmemCols || !prm.rf_omega)
+      return cudaErrorInvalidValue;
+    return launch_rows(prm, grid, s);
+  }
   if (cluster == 2 && prm.share_b) {
     if (prm.checks) return cudaErrorInvalidValue;
     return launch_pair(prm, grid, s);
@@ -1191,7 +1328,7 @@ cudaError_t launch_contract_tc(const TcParams& prm, int form, int cluster, int g
   const int max_nc = (form == TC_F16_3 && prm.share_b) ? kMaxNCWide : kMaxNC;
   if (prm.NC < 16 || prm.NC > max_nc || prm.NC % 16 != 0 || prm.chunk_stages < 1)
     return cudaErrorInvalidValue;
-  if (prm.share_b && form != TC_F16_3) return cudaErrorInvalidValue;
+  if ((prm.share_b || prm.rf) && form != TC_F16_3) return cudaErrorInvalidValue;
   switch (form) {
     case TC_BF16_3: return launch_form<false, 2, 3>(prm, cluster, grid, s);
     case TC_BF16_6: return launch_form<false, 3, 6>(prm, cluster, grid, s);
