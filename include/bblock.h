@@ -206,7 +206,11 @@ int bblock_last_wave_count(const bblock_ctx* ctx);
                                   occurrence and replayed afterwards; 0: plain launches */
 #define BBLOCK_OPT_TC_NC 2     /* tensor-core forms: complex columns per tile, 16, 32 or 48;
                                   the FP16 form's CTA pairs also take 64 or 80 */
-#define BBLOCK_OPT_TC_CHUNK 3  /* tensor-core forms: stages between accumulator drains, 1..8 */
+#define BBLOCK_OPT_TC_CHUNK 3  /* tensor-core forms: stages between accumulator drains, 1..8
+                                  (default 2). Longer intervals are faster and less accurate:
+                                  the accumulator's rounding drift grows with the MMAs it
+                                  collects; the autotuner tries up to 3 (up to 2 in the FP16
+                                  form) */
 #define BBLOCK_OPT_SLABS 4     /* site slabs per job (split of the site sum), 1..4096 */
 #define BBLOCK_OPT_CHECKS 5    /* 1: the tensor-core contraction checks every global index
                                   against its buffer, skips and records violations, and in
