@@ -155,7 +155,7 @@ def phase_columns(path, L, momenta):
     """Phase columns per d3 of the tensor-core GEMM: every momentum, or (row-factored
     path) the distinct x-components n0 mod L."""
     mom = np.asarray(momenta).reshape(-1, 3)
-    return len({int(m[0]) % L for m in mom}) if path == "tc_rows" else len(mom)
+    return len({int(m[0]) % L for m in mom}) if path.startswith("tc_rows") else len(mom)
 
 
 def contraction_df_inst(X, nd, P, pairs):

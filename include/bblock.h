@@ -191,6 +191,7 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 #define BBLOCK_PATH_TC_CLUSTER 2
 #define BBLOCK_PATH_TC_PAIRS 3
 #define BBLOCK_PATH_TC_ROWS 4
+#define BBLOCK_PATH_TC_ROWS_CLUSTER 5   /* row-factored, clusters of 2 sharing each diquark tile */
 int bblock_last_path(const bblock_ctx* ctx);
 
 /* Number of waves the last compute call ran its jobs in: jobs are taken in list order, and
@@ -234,8 +235,12 @@ int bblock_last_wave_count(const bblock_ctx* ctx);
                                        CTAs with N tiles of up to 48 columns; any other value
                                        (the default) runs CTA pairs that share the third-quark
                                        tile of an N tile of up to 80 columns and take adjacent
-                                       128-pair tiles. Index checks and the wait-limit test
-                                       hook use no clusters */
+                                       128-pair tiles. With the row-factored phase
+                                       (BBLOCK_OPT_TC_ROWS): 2, or 0 when every job of a wave
+                                       has at least two d3 tiles, runs clusters that share each
+                                       diquark tile and take adjacent d3 tiles; 1 plain CTAs.
+                                       Index checks and the wait-limit test hook use no
+                                       clusters */
 #define BBLOCK_OPT_CORRUPT_CANARY 9  /* test hook (with BBLOCK_OPT_CHECKS): 1 makes the next
                                        call overwrite its first canary from the host, in
                                        stream order between the fill and the check, once */

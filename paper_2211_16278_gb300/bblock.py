@@ -210,7 +210,7 @@ def bblock_last_wave_count(ctx: Context) -> int:
     return int(load().bblock_last_wave_count(ctx.handle))
 
 
-PATHS = {0: "fp64", 1: "tc", 2: "tc_cluster", 3: "tc_pairs", 4: "tc_rows"}
+PATHS = {0: "fp64", 1: "tc", 2: "tc_cluster", 3: "tc_pairs", 4: "tc_rows", 5: "tc_rows_cluster"}
 
 
 def bblock_last_path(ctx: Context) -> str:

@@ -315,23 +315,35 @@ __device__ __forceinline__ void split_store8(const float (&v)[8], uint8_t* const
 // FP16 number (smaller values keep an absolute error below 2^-25). Round-to-nearest-even is
 // symmetric under negation, so the pieces of -v are the stored pieces with the sign bits
 // (bit 15 of each half) flipped.
+// NG = 8 values (one 16-byte K run per piece) or the first 4 (8 bytes).
+template <int NG = 8>
 __device__ __forceinline__ void split_store8_f16(const float (&v)[8], uint8_t* const (&dst)[2],
                                                  uint8_t* const* neg) {
+  static_assert(NG == 8 || NG == 4, "K runs of 8 or 4 values");
   uint32_t hw[4], lw[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < NG / 2; ++i) {
     const __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);   // .x = low 16 bits
     const float2 hf = __half22float2(h);
     const __half2 l = __floats2half2_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
     hw[i] = *reinterpret_cast<const uint32_t*>(&h);
     lw[i] = *reinterpret_cast<const uint32_t*>(&l);
   }
-  *reinterpret_cast<uint4*>(dst[0]) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-  *reinterpret_cast<uint4*>(dst[1]) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-  if (neg) {
-    constexpr uint32_t m = 0x80008000u;
-    *reinterpret_cast<uint4*>(neg[0]) = make_uint4(hw[0] ^ m, hw[1] ^ m, hw[2] ^ m, hw[3] ^ m);
-    *reinterpret_cast<uint4*>(neg[1]) = make_uint4(lw[0] ^ m, lw[1] ^ m, lw[2] ^ m, lw[3] ^ m);
+  constexpr uint32_t m = 0x80008000u;
+  if (NG == 8) {
+    *reinterpret_cast<uint4*>(dst[0]) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(dst[1]) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    if (neg) {
+      *reinterpret_cast<uint4*>(neg[0]) = make_uint4(hw[0] ^ m, hw[1] ^ m, hw[2] ^ m, hw[3] ^ m);
+      *reinterpret_cast<uint4*>(neg[1]) = make_uint4(lw[0] ^ m, lw[1] ^ m, lw[2] ^ m, lw[3] ^ m);
+    }
+  } else {
+    *reinterpret_cast<uint2*>(dst[0]) = make_uint2(hw[0], hw[1]);
+    *reinterpret_cast<uint2*>(dst[1]) = make_uint2(lw[0], lw[1]);
+    if (neg) {
+      *reinterpret_cast<uint2*>(neg[0]) = make_uint2(hw[0] ^ m, hw[1] ^ m);
+      *reinterpret_cast<uint2*>(neg[1]) = make_uint2(lw[0] ^ m, lw[1] ^ m);
+    }
   }
 }
 
@@ -482,9 +494,10 @@ template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C, bool PROJ, bool 
           bool SHB = false, bool RF = false>
 __device__ __forceinline__ void tc_body(const TcParams& prm) {
   using R = Roles<TF32, SHB ? 1 : C>;
-  static_assert(!RF || (F16 && C == 1 && !CHECKS && !PROJ), "row-factored: FP16, plain CTAs");
+  static_assert(!RF || (F16 && (C == 1 || (C == 2 && !SHB)) && !CHECKS && !PROJ),
+                "row-factored: FP16, plain CTAs or pairs sharing the diquark tile");
   static_assert(!PROJ || (C == 1 && !CHECKS), "the projection runs without clusters or checks");
-  static_assert(!F16 || (!TF32 && LEVELS == 2 && (C == 1 || SHB) && !PROJ),
+  static_assert(!F16 || (!TF32 && LEVELS == 2 && (C == 1 || SHB || RF) && !PROJ),
                 "the FP16 form: two pieces, contraction only, clusters only as CTA pairs");
   static_assert(!SHB || (F16 && C == 2 && !CHECKS), "CTA pairs: the FP16 form, unchecked");
   constexpr bool kShareA = C > 1 && !SHB;          // cluster CTAs share the diquark tile
@@ -653,7 +666,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
         } else if constexpr (RF) {
           // N side: w^{n0 x0} x third quark of the row (idx0, d3); pidx holds n0 (mod L)
           const int idx0 = rr / prm.rf_nc;
-          const int d3 = w.nt * prm.rf_nc + (rr - idx0 * prm.rf_nc);
+          const int d3 = (kShareA ? w.nt * C + (int)rank : w.nt) * prm.rf_nc + (rr - idx0 * prm.rf_nc);
           row_ok = row_used && d3 < nd3 && idx0 < prm.rf_nidx;
           off1 = row_ok ? d3 : 0; s1 = nd3; pidx = row_ok ? prm.rf_n0[idx0] : 0;
         } else {
@@ -832,8 +845,13 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
             }
             uint8_t* const* neg = (is_a || !kTwoMma) ? nullptr : dn;
             if constexpr (F16) {
-              split_store8_f16(re[c], dr, nullptr);
-              split_store8_f16(im[c], di, neg);
+              if (NG == 8) {
+                split_store8_f16<8>(re[c], dr, nullptr);
+                split_store8_f16<8>(im[c], di, neg);
+              } else {
+                split_store8_f16<4>(re[c], dr, nullptr);
+                split_store8_f16<4>(im[c], di, neg);
+              }
             } else if constexpr (TF32) {
               split_store8<TF32, LEVELS>(re[c], dr, nullptr);
               split_store8<TF32, LEVELS>(im[c], di, neg);
@@ -1018,7 +1036,12 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
               tmem_ld16(lead + 3 * NC + i0 * ncol + col, ci);
               tmem_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 16; ++i) { tr[i] += cr[i]; ti[i] += ci[i]; }
+              for (int i = 0; i < 16; i += 2) {
+                const float2 r2 = __fadd2_rn(make_float2(tr[i], tr[i + 1]), make_float2(cr[i], cr[i + 1]));
+                const float2 i2 = __fadd2_rn(make_float2(ti[i], ti[i + 1]), make_float2(ci[i], ci[i + 1]));
+                tr[i] = r2.x; tr[i + 1] = r2.y;
+                ti[i] = i2.x; ti[i + 1] = i2.y;
+              }
               for (int p = 0; p < prm.P; ++p) {
                 if (prm.rf_pidx0[p] != i0) continue;
                 const float2 ph = s_omega[(prm.rf_pn1[p] * x1 + prm.rf_pn2[p] * x2) % prm.L];
@@ -1029,11 +1052,20 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                   tmem_ld16(rp + ncol, ri);
                   tmem_wait_ld();
                 }
+                // run += ph x t, two adjacent columns per packed FMA (each lane rounds as fmaf):
+                //   re = ph.x tr - ph.y ti + re,   im = ph.x ti + ph.y tr + im
+                const float2 phx = make_float2(ph.x, ph.x), phy = make_float2(ph.y, ph.y);
+                const float2 nphy = make_float2(-ph.y, -ph.y);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                  const float a = ch > 0 ? rr[i] : 0.f, b = ch > 0 ? ri[i] : 0.f;
-                  rr[i] = fmaf(ph.x, tr[i], fmaf(-ph.y, ti[i], a));
-                  ri[i] = fmaf(ph.x, ti[i], fmaf(ph.y, tr[i], b));
+                for (int i = 0; i < 16; i += 2) {
+                  const float2 a = ch > 0 ? make_float2(rr[i], rr[i + 1]) : make_float2(0.f, 0.f);
+                  const float2 b = ch > 0 ? make_float2(ri[i], ri[i + 1]) : make_float2(0.f, 0.f);
+                  const float2 t_r = make_float2(tr[i], tr[i + 1]);
+                  const float2 t_i = make_float2(ti[i], ti[i + 1]);
+                  const float2 re = __ffma2_rn(phx, t_r, __ffma2_rn(nphy, t_i, a));
+                  const float2 im = __ffma2_rn(phx, t_i, __ffma2_rn(phy, t_r, b));
+                  rr[i] = re.x; rr[i + 1] = re.y;
+                  ri[i] = im.x; ri[i + 1] = im.y;
                 }
                 tmem_st16(rp, rr);
                 tmem_st16(rp + ncol, ri);
@@ -1095,7 +1127,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
               if (m < M) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                  const int d3 = w.nt * ncol + col + i;
+                  const int d3 = (kShareA ? w.nt * C + (int)rank : w.nt) * ncol + col + i;
                   if (d3 < nd3)
                     J.partial[(((size_t)w.slab * prm.P + p) * M + m) * nd3 + d3] =
                         make_float2(vr[i], vi[i]);
@@ -1153,6 +1185,13 @@ k_contract_tc(const __grid_constant__ TcParams prm) {
 __global__ void __launch_bounds__(Roles<false, 1>::kThreads, 1)
 k_contract_tc_rows(const __grid_constant__ TcParams prm) {
   tc_body<false, 2, 3, false, 1, false, true, false, true>(prm);
+}
+
+// The row-factored FP16 contraction as clusters of 2 that share each diquark tile and take
+// adjacent d3 tiles.
+__global__ void __launch_bounds__(Roles<false, 2>::kThreads, 1)
+k_contract_tc_rows2(const __grid_constant__ TcParams prm) {
+  tc_body<false, 2, 3, false, 2, false, true, false, true>(prm);
 }
 
 // The FP16 form as CTA pairs that share the third-quark tile (clusters of 2).
@@ -1245,13 +1284,36 @@ cudaError_t launch_pair(const TcParams& prm, int grid, cudaStream_t s) {
 }
 
 // The row-factored FP16 contraction: one CTA per SM; the stages, then the w^k table.
-cudaError_t launch_rows(const TcParams& prm, int grid, cudaStream_t s) {
+cudaError_t launch_rows(const TcParams& prm, int cluster, int grid, cudaStream_t s) {
   using Lay = TcLayout<false, 2, true, true>;
   const size_t smem = (size_t)Lay::kStages * Lay::kStageBytes + 128 * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_contract_tc_rows,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = cluster == 2 ? k_contract_tc_rows2 : k_contract_tc_rows;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_contract_tc_rows<<<grid, Roles<false, 1>::kThreads, smem, s>>>(prm);
+  if (cluster == 1) {
+    kern<<<grid, Roles<false, 1>::kThreads, smem, s>>>(prm);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(Roles<false, 2>::kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)grid);
+  int max_clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
+  if (e != cudaSuccess) return e;
+  if (max_clusters < 1) return cudaErrorInvalidConfiguration;
+  const long long want = (grid + 1) / 2;
+  cfg.gridDim = dim3((unsigned)(2 * (want < max_clusters ? want : max_clusters)));
+  e = cudaLaunchKernelEx(&cfg, kern, prm);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -1260,12 +1322,12 @@ cudaError_t launch_rows(const TcParams& prm, int grid, cudaStream_t s) {
 // phase (unchecked).
 cudaError_t launch_form_f16(const TcParams& prm, int cluster, int grid, cudaStream_t s) {
   if (prm.rf) {
-    if (prm.checks || cluster != 1 || prm.share_b || prm.L < 1 || prm.L > 128 ||
+    if (prm.checks || (cluster != 1 && cluster != 2) || prm.share_b || prm.L < 1 || prm.L > 128 ||
         prm.rf_nidx < 1 || prm.rf_nidx > kMaxRfIdx || prm.P > kMaxRfP || prm.rf_spr < 1 ||
         prm.rf_nc < 16 || prm.rf_nc % 16 != 0 || prm.NC != prm.rf_nidx * prm.rf_nc ||
         4 * prm.NC + 2 * prm.P * prm.rf_nc > kTmemCols || !prm.rf_omega)
       return cudaErrorInvalidValue;
-    return launch_rows(prm, grid, s);
+    return launch_rows(prm, cluster, grid, s);
   }
   if (cluster == 2 && prm.share_b) {
     if (prm.checks) return cudaErrorInvalidValue;

@@ -54,7 +54,7 @@ CASES = [
 ]
 
 
-def blocks(torch, bb, inp, rows, nc=0, stream=None, ctx=None):
+def blocks(torch, bb, inp, rows, nc=0, stream=None, ctx=None, cluster=0):
     w = inp.workload
     dev = torch.device("cuda:0")
     V = torch.from_numpy(inp.V).to(dev)
@@ -64,6 +64,7 @@ def blocks(torch, bb, inp, rows, nc=0, stream=None, ctx=None):
         ctx = bb.bblock_create(w.L, w.n_ev, max(inp.ndil[0]), "fp16x3")
         bb.bblock_set_option(ctx, "tc_rows", rows)
         bb.bblock_set_option(ctx, "tc_nc", nc)
+        bb.bblock_set_option(ctx, "tc_cluster", cluster)
     B = bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, stream=stream)
     bb.bblock_status(ctx)
     out = B.cpu().numpy()
@@ -85,16 +86,17 @@ def distinct_n0(L, mom):
 
 @pytest.mark.parametrize("nc", [0, 16, 32, 48])
 @pytest.mark.parametrize("case", range(len(CASES)))
-def test_rows_match_oracle(env, case, nc):
+@pytest.mark.parametrize("cluster", [1, 0])
+def test_rows_match_oracle(env, case, nc, cluster):
     torch, bb = env
     L, n_ev, nd, n_t, mom, spins, coeffs = CASES[case]
     k = distinct_n0(L, mom)
     if nc and (k * nc > 48 or 4 * k * nc + 2 * len(mom) * nc > 512):
         pytest.skip("tile does not fit the row-factored layout")
     inp = workloads.custom(L, n_ev, nd, n_t, mom, spins, coeffs, seed=9000 + case)
-    got = blocks(torch, bb, inp, rows=1, nc=nc)
+    got = blocks(torch, bb, inp, rows=1, nc=nc, cluster=cluster)
     err = rel(got, oracle_blocks(inp))
-    print(f"fp16x3 rows case {case} nc {nc}: rel. Frobenius error {err:.3e}")
+    print(f"fp16x3 rows case {case} nc {nc} cluster {cluster}: rel. Frobenius error {err:.3e}")
     assert np.all(np.isfinite(got)) and err <= TOL
 
 
@@ -146,3 +148,26 @@ def test_rows_batch_uneven_dilution(env):
         ref = oracle.bblock(L, V, *ph, C4_MOM, spins, coeffs)
         assert rel(job[4].cpu().numpy(), ref) <= TOL
     bb.bblock_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_rows_in_clusters_sharing_the_diquark_tile(env, case):
+    """Clusters of two CTAs that build half of each diquark tile each and take adjacent d3
+    tiles (BBLOCK_OPT_TC_CLUSTER = 2): the same blocks as the plain row-factored CTAs, to the
+    form's tolerance, including jobs with an odd number of d3 tiles."""
+    torch, bb = env
+    L, n_ev, nd, n_t, mom, spins, coeffs = CASES[case]
+    inp = workloads.custom(L, n_ev, nd, n_t, mom, spins, coeffs, seed=9400 + case)
+    w = inp.workload
+    ctx = bb.bblock_create(w.L, w.n_ev, max(nd), "fp16x3")
+    bb.bblock_set_option(ctx, "tc_rows", 1)
+    bb.bblock_set_option(ctx, "tc_cluster", 2)
+    got = blocks(torch, bb, inp, 1, ctx=ctx)
+    assert bb.bblock_last_path(ctx) == "tc_rows_cluster"
+    bb.bblock_destroy(ctx)
+    ref = oracle_blocks(inp)
+    err = rel(got, ref)
+    print(f"fp16x3 rows in clusters case {case}: rel. Frobenius error {err:.3e}")
+    assert np.all(np.isfinite(got)) and err <= TOL
+    plain = blocks(torch, bb, inp, rows=1, cluster=1)
+    assert rel(got, plain) <= 2 * TOL
