@@ -66,13 +66,21 @@ typedef enum {
                             of FP32, about 48 significant bits) on the FP32 pipe; FP64 only
                             for the input conversion, the phases and the slab reduction;
                             parity target 1e-12 */
-  BBLOCK_FP16X3 = 4      /* contraction on the tensor cores with FP16 operands split in two
+  BBLOCK_FP16X3 = 4,     /* contraction on the tensor cores with FP16 operands split in two
                             (hi = rn16(v), lo = rn16(v - hi), about 22 bits), 3 products
                             (hi hi, hi lo, lo hi), FP32 accumulate; the operands are scaled
                             by powers of two chosen per job from the largest field entry of
                             each quark line, so FP16's range never overflows, and the FP64
                             slab reduction removes the scale exactly; projection in FP32 FMA;
                             parity target 1e-6 */
+  BBLOCK_OZAKI = 5       /* FP64-accurate contraction on the BF16 tensor cores (Ozaki scheme):
+                            the double-float projection's diquark and phase-folded third
+                            quark, scaled by powers of two per row and column of each site
+                            slab, split into 7 BF16 digits of 8 bits; the 28 digit products
+                            down to 2^-56 of the scales are summed exactly (levels 0-3, one
+                            FP32 accumulator each, drained every 240 K elements) or to FP32
+                            rounding (levels 4-6) into double-float running sums; FP64 slab
+                            reduction; parity target 1e-12 */
 } bblock_precision;
 
 typedef struct bblock_ctx bblock_ctx;
@@ -192,6 +200,7 @@ int bblock_last_launch_count(const bblock_ctx* ctx);
 #define BBLOCK_PATH_TC_PAIRS 3
 #define BBLOCK_PATH_TC_ROWS 4
 #define BBLOCK_PATH_TC_ROWS_CLUSTER 5   /* row-factored, clusters of 2 sharing each diquark tile */
+#define BBLOCK_PATH_OZAKI 6             /* the BBLOCK_OZAKI contraction */
 int bblock_last_path(const bblock_ctx* ctx);
 
 /* Number of waves the last compute call ran its jobs in: jobs are taken in list order, and
@@ -240,7 +249,10 @@ int bblock_last_wave_count(const bblock_ctx* ctx);
                                        has at least two d3 tiles, runs clusters that share each
                                        diquark tile and take adjacent d3 tiles; 1 plain CTAs.
                                        Index checks and the wait-limit test hook use no
-                                       clusters */
+                                       clusters. BBLOCK_OZAKI: 1, 2, 3 or 4 CTAs sharing each
+                                       diquark tile across adjacent N tiles (results bitwise
+                                       those of 1); 0 (default): 2 unless the ragged last
+                                       clusters pad the N tiles by more than 20 %, else 1 */
 #define BBLOCK_OPT_CORRUPT_CANARY 9  /* test hook (with BBLOCK_OPT_CHECKS): 1 makes the next
                                        call overwrite its first canary from the host, in
                                        stream order between the fill and the check, once */

@@ -27,7 +27,7 @@ ERRORS = {
     -6: "BBLOCK_ERR_DEVICE_FLAG",
     -7: "BBLOCK_ERR_TOO_LARGE",
 }
-PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16": 2, "df64": 3, "fp16x3": 4}
+PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16": 2, "df64": 3, "fp16x3": 4, "ozaki": 5}
 
 # Every symbol include/bblock.h declares.
 EXPORTED = (
@@ -210,7 +210,8 @@ def bblock_last_wave_count(ctx: Context) -> int:
     return int(load().bblock_last_wave_count(ctx.handle))
 
 
-PATHS = {0: "fp64", 1: "tc", 2: "tc_cluster", 3: "tc_pairs", 4: "tc_rows", 5: "tc_rows_cluster"}
+PATHS = {0: "fp64", 1: "tc", 2: "tc_cluster", 3: "tc_pairs", 4: "tc_rows", 5: "tc_rows_cluster",
+         6: "ozaki"}
 
 
 def bblock_last_path(ctx: Context) -> str:

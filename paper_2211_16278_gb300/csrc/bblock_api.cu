@@ -26,6 +26,7 @@ struct bblock_ctx {
   std::vector<int32_t> phase_mom;
   double2* d_phase = nullptr;     // FP64 phases [n_mom][X], then their FP32 copy
   float2* d_phase_f = nullptr;
+  float4* d_phase_df = nullptr;    // Ozaki form: the phases as double-float float4
   size_t phase_cap = 0;
   int* d_mom = nullptr;
   size_t mom_cap = 0;
@@ -192,7 +193,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // The FP64 and double-float forms share fields, tiles, units and the FP64 reduction.
 bool fp64_like(const bblock_config& cfg) {
-  return cfg.precision == BBLOCK_FP64 || cfg.precision == BBLOCK_DF64;
+  return cfg.precision == BBLOCK_FP64 || cfg.precision == BBLOCK_DF64 ||
+         cfg.precision == BBLOCK_OZAKI;
 }
 
 // Workspace one wave of jobs may take: the caller's limit, else half the free memory seen at
@@ -338,14 +340,20 @@ int ensure_phase(bblock_ctx* c, const int32_t* momenta, int n_mom, cudaStream_t 
   std::vector<int32_t> key(momenta, momenta + 3 * n_mom);
   if (c->d_phase && key == c->phase_mom) return BBLOCK_OK;
   const size_t n_ph = (size_t)c->X * n_mom;
+  const bool oz = c->cfg.precision == BBLOCK_OZAKI;
+  const size_t df_ofs = align_up((sizeof(double2) + sizeof(float2)) * n_ph, 256);
   int rc = grow_device(c, reinterpret_cast<char**>(&c->d_phase), &c->phase_cap,
-                       (sizeof(double2) + sizeof(float2)) * n_ph);
+                       df_ofs + (oz ? sizeof(float4) * n_ph : 0));
   if (rc) return rc;
   c->d_phase_f = reinterpret_cast<float2*>(c->d_phase + n_ph);
+  c->d_phase_df = oz ? reinterpret_cast<float4*>(reinterpret_cast<char*>(c->d_phase) + df_ofs)
+                     : nullptr;
   rc = grow_device(c, reinterpret_cast<char**>(&c->d_mom), &c->mom_cap, sizeof(int) * 3 * n_mom);
   if (rc) return rc;
   CK(c, cudaMemcpyAsync(c->d_mom, momenta, sizeof(int) * 3 * n_mom, cudaMemcpyHostToDevice, s));
   CK(c, timed_launch(c, K_PHASE, s, [&] { return launch_phase_table(c->cfg.L, n_mom, c->d_mom, c->d_phase, c->d_phase_f, s); }));
+  if (oz)
+    CK(c, timed_launch(c, K_PHASE, s, [&] { return launch_phase_df(c->d_phase, c->d_phase_df, (long long)n_ph, s); }));
   // the host momentum array may be reused by the caller right after return
   CK(c, cudaStreamSynchronize(s));
   c->phase_mom = key;
@@ -906,12 +914,33 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
 }
 
 // The whole launch sequence for a list of jobs sharing momenta and spin operator.
+// Ozaki form: clusters of C CTAs share each diquark tile across C adjacent N tiles; each
+// builds 1/C of the tile's rows, with shorter per-thread chains, which sets the stage time.
+// Measured on GB300 (L = 32, 9 momenta, N_dil 32-64): pairs are the fastest, 1.6x the plain
+// CTA; clusters of 3 and 4 are 10 % and 3 % slower than pairs (fewer resident CTAs: 138 and
+// 144 of 152 SMs, and N tiles padded to a multiple of C). Auto: pairs unless their ragged
+// last clusters pad the N tiles by more than 20 %.
+int oz_cluster_for(const bblock_ctx* c, const std::vector<JobIn>& jobs, size_t b, size_t e,
+                   int P_launch, int nc) {
+  if (c->opt_tc_cluster >= 1 && c->opt_tc_cluster <= 4) return c->opt_tc_cluster;
+  long long tiles = 0, padded = 0;
+  for (size_t k = b; k < e; ++k) {
+    const long long nt = ((long long)P_launch * jobs[k].nd[2] + nc - 1) / nc;
+    const long long mt = ((long long)jobs[k].nd[0] * jobs[k].nd[1] + kOzM - 1) / kOzM;
+    tiles += mt * nt;
+    padded += mt * ((nt + 1) / 2) * 2;
+  }
+  return tiles > 0 && (double)(padded - tiles) / tiles <= 0.2 ? 2 : 1;
+}
+
 int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momenta, int n_mom,
              const int32_t* spin_idx, const double* coeffs, int n_spin, int per_mom,
              cudaStream_t s) {
   c->last_launches = 0;
   c->last_waves = 0;
-  c->last_path = fp64_like(c->cfg) ? BBLOCK_PATH_FP64 : -1;
+  c->last_path = c->cfg.precision == BBLOCK_OZAKI ? BBLOCK_PATH_OZAKI
+                 : fp64_like(c->cfg)               ? BBLOCK_PATH_FP64
+                                                   : -1;
   c->last_stream = s;
   c->call_tab_bytes = 0;
   if (jobs.empty() || n_mom == 0) return BBLOCK_OK;
@@ -923,16 +952,38 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
   rc = ensure_phase(c, momenta, n_mom, s);
   if (rc) return rc;
   if (!fp64_like(c->cfg)) return run_jobs_tc(c, jobs, sp, n_mom, per_mom, s);
-  const bool df = c->cfg.precision == BBLOCK_DF64;
+  // the Ozaki form runs on the double-float form's converted inputs and fields
+  const bool oz = c->cfg.precision == BBLOCK_OZAKI;
+  const bool df = c->cfg.precision == BBLOCK_DF64 || oz;
 
   const int X = c->X, rows = c->rows, n_ev = c->cfg.n_ev;
   const int n3_fields = sp.n_pairs * sp.n_coef_sets;
-  const int P_launch =
-      per_mom ? 1 : p_group_size(n_mom, c->cfg.precision == BBLOCK_DF64 ? kMaxPGroupDf : kMaxPGroup);
-  const int xc = fp64_sites_per_chunk(sp.n_pairs);
-  const Fp64Tile tl = fp64_tile_for(P_launch);  // one tile shape for every momentum group
-  const int ctas = fp64_contract_ctas_per_sm(P_launch, tl.rn, sp.n_pairs) * c->num_sms;
+  // momenta per contraction launch: the Ozaki form takes them all as N columns
+  const int P_launch = per_mom ? 1
+                       : oz    ? n_mom
+                               : p_group_size(n_mom, c->cfg.precision == BBLOCK_DF64 ? kMaxPGroupDf
+                                                                                     : kMaxPGroup);
+  const int xc = oz ? 1 : fp64_sites_per_chunk(sp.n_pairs);
+  const Fp64Tile tl = fp64_tile_for(oz ? 1 : P_launch);  // one tile shape for every momentum group
+  // Ozaki form: units run one per CTA (clusters: one per cluster of oz_cl CTAs)
+  const int ctas = oz ? c->num_sms : fp64_contract_ctas_per_sm(P_launch, tl.rn, sp.n_pairs) * c->num_sms;
   const int max_slabs = 64;
+  const int oz_nc = c->opt_tc_nc > 0 && c->opt_tc_nc <= kOzMaxNC ? c->opt_tc_nc : kOzMaxNC;
+  int oz_cl = 1;   // Ozaki form: CTAs per cluster of the current wave
+  // M tiles and N tiles (Ozaki form: clusters of oz_cl N tiles) of a job's contraction
+  auto job_tiles = [&](const JobIn& j, int& mt, int& nt) {
+    if (oz) {
+      mt = (j.nd[0] * j.nd[1] + kOzM - 1) / kOzM;
+      nt = ((P_launch * j.nd[2] + oz_nc - 1) / oz_nc + oz_cl - 1) / oz_cl;
+    } else {
+      mt = (j.nd[0] * j.nd[1] + 16 * tl.rm - 1) / (16 * tl.rm);
+      nt = (j.nd[2] + 16 * tl.rn - 1) / (16 * tl.rn);
+    }
+  };
+  // Ozaki form: the column maxima of every job, [n_slab][nd1 + nd2 + nd3] floats
+  auto oz_bytes = [&](const JobIn& j, int n_slab) -> size_t {
+    return oz ? align_up((size_t)n_slab * (j.nd[0] + j.nd[1] + j.nd[2]) * sizeof(float), 256) : 0;
+  };
 
   // double-float inputs of a job: V and the three phi_i as float4 planes
   auto df_in_bytes = [&](const JobIn& j) -> size_t {
@@ -947,7 +998,7 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
   auto job_bytes = [&](const JobIn& j, int n_slab) {
     size_t f = (size_t)rows * (sp.n1 * j.nd[0] + sp.n2 * j.nd[1] + n3_fields * j.nd[2]) * sizeof(double2);
     size_t p = (size_t)n_slab * n_mom * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(double2);
-    return align_up(f, 256) + align_up(p, 256) + df_in_bytes(j) + canary_bytes;
+    return align_up(f, 256) + align_up(p, 256) + df_in_bytes(j) + canary_bytes + oz_bytes(j, n_slab);
   };
 
   size_t job_idx = 0;
@@ -962,27 +1013,36 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
     }
     ++c->last_waves;
     const int nj = (int)(end - job_idx);
+    if (oz) oz_cl = oz_cluster_for(c, jobs, job_idx, end, P_launch, oz_nc);
     long long tiles = 0;
     int max_nd3 = 0, max_ndf = 0;
     long long max_elems = 0;
     for (size_t k = job_idx; k < end; ++k) {
       const JobIn& j = jobs[k];
-      tiles += (long long)((j.nd[0] * j.nd[1] + 16 * tl.rm - 1) / (16 * tl.rm)) *
-               ((j.nd[2] + 16 * tl.rn - 1) / (16 * tl.rn));
+      int mt, nt;
+      job_tiles(j, mt, nt);
+      tiles += (long long)mt * nt;
       max_nd3 = std::max(max_nd3, j.nd[2]);
       for (int i = 0; i < 3; ++i) max_ndf = std::max(max_ndf, j.nd[i]);
       max_elems = std::max(max_elems, (long long)n_mom * j.nd[0] * j.nd[1] * j.nd[2]);
     }
+    const int unit_slots = oz ? ctas / oz_cl : ctas;
     int n_slab = c->opt_slabs > 0 ? std::min(c->opt_slabs, (X + xc - 1) / xc)
-                                   : choose_slabs(tiles, ctas, X, xc, max_slabs);
+                                   : choose_slabs(tiles, unit_slots, X, xc, max_slabs);
     int sites_per_slab = (X + n_slab - 1) / n_slab;
     sites_per_slab = (sites_per_slab + xc - 1) / xc * xc;
     n_slab = (X + sites_per_slab - 1) / sites_per_slab;
 
-    size_t ws_need = 0;
-    for (size_t k = job_idx; k < end; ++k) ws_need += job_bytes(jobs[k], n_slab);
+    size_t ws_need = 0, oz_need = 0;
+    for (size_t k = job_idx; k < end; ++k) {
+      ws_need += job_bytes(jobs[k], n_slab);
+      oz_need += oz_bytes(jobs[k], n_slab);
+    }
     rc = grow_device(c, &c->d_ws, &c->ws_cap, ws_need);
     if (rc) return rc;
+    // Ozaki form: every job's column maxima in one block at the end (one memset)
+    char* oz_base = c->d_ws + (ws_need - oz_need);
+    std::vector<OzMaxSeg> ozsegs;
 
     // field and job tables
     std::vector<ProjField> fields;
@@ -1063,10 +1123,24 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       base += align_up((size_t)n_slab * n_mom * j.nd[0] * j.nd[1] * j.nd[2] * sizeof(double2), 256);
       canary(base);
       ws = base;
-      const int m_tiles = (j.nd[0] * j.nd[1] + 16 * tl.rm - 1) / (16 * tl.rm);
-      const int n_tiles = (j.nd[2] + 16 * tl.rn - 1) / (16 * tl.rn);
+      int m_tiles, n_tiles;
+      job_tiles(j, m_tiles, n_tiles);
+      float* oz_max = nullptr;
+      if (oz) {
+        oz_max = reinterpret_cast<float*>(oz_base);
+        oz_base += oz_bytes(j, n_slab);
+        const int stride = j.nd[0] + j.nd[1] + j.nd[2];
+        auto seg = [&](const double2* q, int nd, int off) {
+          ozsegs.push_back(OzMaxSeg{reinterpret_cast<const float4*>(q), oz_max, nd, off, stride});
+        };
+        for (int sl = 0; sl < sp.n1; ++sl) seg(q1[sl], j.nd[0], 0);
+        for (int sl = 0; sl < sp.n2; ++sl) seg(q2[sl], j.nd[1], j.nd[0]);
+        for (int set = 0; set < sp.n_coef_sets; ++set)
+          for (int pr = 0; pr < sp.n_pairs; ++pr) seg(q3[set][pr], j.nd[2], j.nd[0] + j.nd[1]);
+      }
       for (int set = 0; set < sp.n_coef_sets; ++set) {
         ContractJob& cj = cjobs[set][k];
+        cj.oz_max = oz_max;
         for (int i = 0; i < 4; ++i) { cj.q1[i] = q1[i]; cj.q2[i] = q2[i]; }
         for (int pr = 0; pr < sp.n_pairs; ++pr) cj.q3[pr] = q3[set][pr];
         cj.partial = partial;
@@ -1097,12 +1171,14 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
     const size_t jbytes = align_up((size_t)nj * sizeof(ContractJob), 256);
     const size_t sofs = fbytes + jbytes * sp.n_coef_sets;
     const size_t cofs = sofs + align_up(segs.size() * sizeof(DfConvSeg), 256);
-    std::vector<char> tab(cofs + canaries.size() * sizeof(uint32_t*));
+    const size_t zofs = cofs + align_up(canaries.size() * sizeof(uint32_t*), 256);
+    std::vector<char> tab(zofs + ozsegs.size() * sizeof(OzMaxSeg));
     memcpy(tab.data(), fields.data(), fields.size() * sizeof(ProjField));
     for (int set = 0; set < sp.n_coef_sets; ++set)
       memcpy(tab.data() + fbytes + jbytes * set, cjobs[set].data(), (size_t)nj * sizeof(ContractJob));
     if (!segs.empty()) memcpy(tab.data() + sofs, segs.data(), segs.size() * sizeof(DfConvSeg));
     if (!canaries.empty()) memcpy(tab.data() + cofs, canaries.data(), canaries.size() * sizeof(uint32_t*));
+    if (!ozsegs.empty()) memcpy(tab.data() + zofs, ozsegs.data(), ozsegs.size() * sizeof(OzMaxSeg));
     rc = upload_tables(c, tab.data(), tab.size(), s);
     if (rc) return rc;
     const ProjField* d_fields = reinterpret_cast<const ProjField*>(c->d_tab);
@@ -1127,6 +1203,14 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       return df ? launch_project_df(d_fields, (int)fields.size(), rows, n_ev, max_ndf, s)
                 : launch_project_fp64(d_fields, (int)fields.size(), rows, n_ev, max_ndf, s);
     }));
+    if (oz) {
+      // the slabs' column maxima of every field, from which the contraction takes its scales
+      CK(c, cudaMemsetAsync(c->d_ws + (ws_need - oz_need), 0, oz_need, s));
+      CK(c, timed_launch(c, K_PROJECT, s, [&] {
+        return launch_oz_colmax(reinterpret_cast<const OzMaxSeg*>(c->d_tab + zofs),
+                                (int)ozsegs.size(), X, sites_per_slab, s);
+      }));
+    }
 
     ContractParams prm{};
     prm.n_jobs = nj;
@@ -1139,8 +1223,23 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
     prm.phase = c->d_phase;
     prm.P_total = n_mom;
     prm.status = c->d_status;
+    prm.phase_df = c->d_phase_df;
+    prm.NC = oz_nc;
+    prm.wait_limit = c->opt_wait_us > 0 ? (long long)c->opt_wait_us * c->cycles_per_us
+                                        : 4000000000LL;
     const int grid = (int)std::min<long long>(unit, ctas);
-    if (per_mom) {
+    if (oz) {
+      // every momentum as N columns of one launch (one launch per momentum with per-momentum
+      // coefficient sets)
+      for (int set = 0; set < sp.n_coef_sets; ++set) {
+        prm.jobs = reinterpret_cast<const ContractJob*>(c->d_tab + fbytes + jbytes * set);
+        prm.p0 = per_mom ? set : 0;
+        prm.P = per_mom ? 1 : n_mom;
+        CK(c, timed_launch(c, K_CONTRACT, s, [&] {
+          return launch_contract_oz(prm, oz_cl, (int)std::min<long long>(unit, unit_slots), s);
+        }));
+      }
+    } else if (per_mom) {
       for (int p = 0; p < n_mom; ++p) {
         prm.jobs = reinterpret_cast<const ContractJob*>(c->d_tab + fbytes + jbytes * p);
         prm.p0 = p;
@@ -1300,6 +1399,19 @@ CallPlan plan_call(const bblock_ctx* c, int n_t, const int nd[3], int n_mom, int
                    int nc_opt, int chunk_opt, int slabs_opt) {
   CallPlan pl;
   const int X = c->X;
+  if (c->cfg.precision == BBLOCK_OZAKI) {
+    // units (job, 128-row tile, N tile over every momentum's columns, slab)
+    const int nc = nc_opt > 0 && nc_opt <= kOzMaxNC ? nc_opt : kOzMaxNC;
+    const long long nt = ((long long)n_mom * nd[2] + nc - 1) / nc;
+    const long long tiles = (long long)n_t * ((nd[0] * nd[1] + kOzM - 1) / kOzM) * nt;
+    pl.nc = nc;
+    pl.n_slab = slabs_opt > 0 ? std::min(slabs_opt, X) : choose_slabs(tiles, c->num_sms, X, 1, 64);
+    const int sps = (X + pl.n_slab - 1) / pl.n_slab;
+    pl.n_slab = (X + sps - 1) / sps;
+    pl.units = tiles * pl.n_slab;
+    pl.pad = (double)(nt * nc) / ((double)n_mom * nd[2]) - 1.0;
+    return pl;
+  }
   if (fp64_like(c->cfg)) {
     const int P = p_group_size(n_mom, c->cfg.precision == BBLOCK_DF64 ? kMaxPGroupDf : kMaxPGroup);
     const Fp64Tile tl = fp64_tile_for(P);
@@ -1361,6 +1473,7 @@ int form_code(const bblock_config& cfg) {
   if (cfg.precision == BBLOCK_DF64) return 5;
   if (cfg.precision == BBLOCK_TF32X3) return 4;
   if (cfg.precision == BBLOCK_FP16X3) return 6;
+  if (cfg.precision == BBLOCK_OZAKI) return 7;
   return cfg.bf16_products == 3 ? 1 : cfg.bf16_products == 9 ? 3 : 2;
 }
 
@@ -1393,7 +1506,7 @@ int bblock_create(bblock_ctx** out, const bblock_config* cfg) {
   const long long X = (long long)cfg->L * cfg->L * cfg->L;
   if (cfg->n_ev < 1 || cfg->n_ev > 3 * X) return BBLOCK_ERR_INVALID_ARG;
   if (cfg->max_ndil < 1 || cfg->max_ndil > 256) return BBLOCK_ERR_INVALID_ARG;
-  if (cfg->precision < BBLOCK_FP64 || cfg->precision > BBLOCK_FP16X3) return BBLOCK_ERR_INVALID_ARG;
+  if (cfg->precision < BBLOCK_FP64 || cfg->precision > BBLOCK_OZAKI) return BBLOCK_ERR_INVALID_ARG;
   if (cfg->precision == BBLOCK_BF16_SPLIT && cfg->bf16_products != 3 && cfg->bf16_products != 6 &&
       cfg->bf16_products != 9)
     return BBLOCK_ERR_INVALID_ARG;
@@ -1949,7 +2062,9 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       c->opt_fail_alloc = value;
       return BBLOCK_OK;
     case BBLOCK_OPT_TC_CLUSTER:
-      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8) break;
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 &&
+          !(c->cfg.precision == BBLOCK_OZAKI && value == 3))
+        break;
       c->opt_tc_cluster = value;
       return BBLOCK_OK;
     case BBLOCK_OPT_TC_ROWS:

@@ -67,6 +67,9 @@ struct ContractJob {
   const double2* q3[kMaxPairs];  // folded line-3 field per (alpha, beta) pair
   double2* partial;              // [n_slab][P_total][nd1*nd2][nd3]
   double2* B;                    // [P_total][nd1][nd2][nd3]
+  // Ozaki form: column maxima of the job's line-1, line-2 and line-3 fields per site slab,
+  // [n_slab][nd1 + nd2 + nd3] (|Re| + |Im| of the high parts); null in the other forms
+  const float* oz_max;
   int nd1, nd2, nd3;
   int m_tiles, n_tiles;
   long long unit_begin;          // first global work-unit index of this job
@@ -86,6 +89,13 @@ struct ContractParams {
   int p0;                        // first momentum of this launch
   int P_total;
   int* status;
+  // Ozaki form: the phases as double-float float4 (re.h, re.l, im.h, im.l), [P_total][X];
+  // P momenta per launch (columns n = p * nd3 + d3, p < P), NC complex columns per N tile,
+  // and the limit of every bounded wait in SM cycles
+  const float4* phase_df;
+  int P;
+  int NC;
+  long long wait_limit;
 };
 
 // Tiles of the FP64 contraction for a momentum count (per launch).
@@ -246,6 +256,31 @@ cudaError_t launch_convert_df(const DfConvSeg* d_segs, int n_segs, long long max
 cudaError_t launch_project_df(const ProjField* d_fields, int n_fields, int rows, int n_ev,
                               int max_nd, cudaStream_t s);
 int fp64_contract_ctas_per_sm(int P, int rn, int n_pairs);
+
+// ---------------------------------------------------------------- Ozaki form
+
+// FP64-accurate contraction on the BF16 tensor cores (oz_contract.cu): units (job, 128-row
+// M tile, NC-column N tile over the launch's P * nd3 columns, site slab); fields are
+// double-float float4 planes, partial blocks are written in FP64 like the FP64 form's.
+constexpr int kOzMaxNC = 48;
+constexpr int kOzM = 128;
+// cluster: 1 (plain CTAs) or 2, 3, 4 CTAs sharing each diquark tile; grid: units (clusters)
+// wanted at once, capped at the clusters that can be resident
+cudaError_t launch_contract_oz(const ContractParams& p, int cluster, int grid, cudaStream_t s);
+// One field's contribution to a job's column maxima: max over the slab's rows (x, c) of
+// |Re| + |Im| (high parts) of column d, max-ed into out[slab * stride + col_off + d]
+// (zeroed before).
+struct OzMaxSeg {
+  const float4* field;           // [3X][nd] double-float
+  float* out;
+  int nd;
+  int col_off;
+  int stride;
+};
+cudaError_t launch_oz_colmax(const OzMaxSeg* d_segs, int n_segs, int X, int sites_per_slab,
+                             cudaStream_t s);
+// FP64 phases to double-float float4, n elements
+cudaError_t launch_phase_df(const double2* ph, float4* out, long long n, cudaStream_t s);
 cudaError_t launch_reduce_slabs(const ContractJob* d_jobs, int n_jobs, int n_slab, int P_total,
                                 long long max_elems, cudaStream_t s);
 

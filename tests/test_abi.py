@@ -81,7 +81,8 @@ def test_binding_options_and_precisions_match_header():
     enum = re.search(r"typedef enum \{([^}]*)\} bblock_precision;", text, re.S).group(1)
     precisions = {m.group(1).lower(): int(m.group(2))
                   for m in re.finditer(r"BBLOCK_(\w+)\s*=\s*(\d+)", enum)}
-    assert precisions == {"fp64": 0, "tf32x3": 1, "bf16_split": 2, "df64": 3, "fp16x3": 4}
-    for name in ("fp64", "tf32x3", "df64", "fp16x3"):
+    assert precisions == {"fp64": 0, "tf32x3": 1, "bf16_split": 2, "df64": 3, "fp16x3": 4,
+                          "ozaki": 5}
+    for name in ("fp64", "tf32x3", "df64", "fp16x3", "ozaki"):
         assert bbm.PRECISIONS[name] == precisions[name]
     assert bbm.PRECISIONS["bf16"] == precisions["bf16_split"]

@@ -15,8 +15,8 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 FORMS = [("fp64", 6, 1e-12), ("df64", 6, 1e-12), ("bf16", 6, 1e-6), ("tf32x3", 6, 1e-6),
-         ("bf16", 9, 1e-6), ("fp16x3", 6, 1e-6)]
-IDS = ["fp64", "df64", "bf16x6", "tf32x3", "bf16x9", "fp16x3"]
+         ("bf16", 9, 1e-6), ("fp16x3", 6, 1e-6), ("ozaki", 6, 1e-12)]
+IDS = ["fp64", "df64", "bf16x6", "tf32x3", "bf16x9", "fp16x3", "ozaki"]
 
 
 @pytest.fixture(scope="module")
