@@ -980,9 +980,12 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
       nt = (j.nd[2] + 16 * tl.rn - 1) / (16 * tl.rn);
     }
   };
-  // Ozaki form: the column maxima of every job, [n_slab][nd1 + nd2 + nd3] floats
+  // Ozaki form: the column and row maxima of every job, [n_slab][nd1 + nd2 + nd3] and
+  // [n_slab][nd1 nd2] floats
   auto oz_bytes = [&](const JobIn& j, int n_slab) -> size_t {
-    return oz ? align_up((size_t)n_slab * (j.nd[0] + j.nd[1] + j.nd[2]) * sizeof(float), 256) : 0;
+    return oz ? align_up((size_t)n_slab * (j.nd[0] + j.nd[1] + j.nd[2] + j.nd[0] * j.nd[1]) *
+                             sizeof(float), 256)
+              : 0;
   };
 
   // double-float inputs of a job: V and the three phi_i as float4 planes
@@ -1130,13 +1133,14 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
         oz_max = reinterpret_cast<float*>(oz_base);
         oz_base += oz_bytes(j, n_slab);
         const int stride = j.nd[0] + j.nd[1] + j.nd[2];
-        auto seg = [&](const double2* q, int nd, int off) {
-          ozsegs.push_back(OzMaxSeg{reinterpret_cast<const float4*>(q), oz_max, nd, off, stride});
+        auto seg = [&](const double2* q, int nd, int off, int modulus) {
+          ozsegs.push_back(
+              OzMaxSeg{reinterpret_cast<const float4*>(q), oz_max, nd, off, stride, modulus});
         };
-        for (int sl = 0; sl < sp.n1; ++sl) seg(q1[sl], j.nd[0], 0);
-        for (int sl = 0; sl < sp.n2; ++sl) seg(q2[sl], j.nd[1], j.nd[0]);
+        for (int sl = 0; sl < sp.n1; ++sl) seg(q1[sl], j.nd[0], 0, 0);
+        for (int sl = 0; sl < sp.n2; ++sl) seg(q2[sl], j.nd[1], j.nd[0], 0);
         for (int set = 0; set < sp.n_coef_sets; ++set)
-          for (int pr = 0; pr < sp.n_pairs; ++pr) seg(q3[set][pr], j.nd[2], j.nd[0] + j.nd[1]);
+          for (int pr = 0; pr < sp.n_pairs; ++pr) seg(q3[set][pr], j.nd[2], j.nd[0] + j.nd[1], 1);
       }
       for (int set = 0; set < sp.n_coef_sets; ++set) {
         ContractJob& cj = cjobs[set][k];
@@ -1229,6 +1233,11 @@ int run_jobs(bblock_ctx* c, const std::vector<JobIn>& jobs, const int32_t* momen
                                         : 4000000000LL;
     const int grid = (int)std::min<long long>(unit, ctas);
     if (oz) {
+      // the diquark's row maxima (from the line-1 and line-2 fields of any coefficient set)
+      int max_mt = 0;
+      for (int k = 0; k < nj; ++k) max_mt = std::max(max_mt, cjobs[0][k].m_tiles);
+      prm.jobs = reinterpret_cast<const ContractJob*>(c->d_tab + fbytes);
+      CK(c, timed_launch(c, K_PROJECT, s, [&] { return launch_oz_rowmax(prm, max_mt, s); }));
       // every momentum as N columns of one launch (one launch per momentum with per-momentum
       // coefficient sets)
       for (int set = 0; set < sp.n_coef_sets; ++set) {

@@ -67,9 +67,10 @@ struct ContractJob {
   const double2* q3[kMaxPairs];  // folded line-3 field per (alpha, beta) pair
   double2* partial;              // [n_slab][P_total][nd1*nd2][nd3]
   double2* B;                    // [P_total][nd1][nd2][nd3]
-  // Ozaki form: column maxima of the job's line-1, line-2 and line-3 fields per site slab,
-  // [n_slab][nd1 + nd2 + nd3] (|Re| + |Im| of the high parts); null in the other forms
-  const float* oz_max;
+  // Ozaki form: per site slab, the column maxima of the job's line-1 and line-2 fields
+  // (|Re| + |Im|) and line-3 fields (modulus) of the high parts, [n_slab][nd1 + nd2 + nd3],
+  // then the diquark's row maxima, [n_slab][nd1 nd2]; null in the other forms
+  float* oz_max;
   int nd1, nd2, nd3;
   int m_tiles, n_tiles;
   long long unit_begin;          // first global work-unit index of this job
@@ -276,9 +277,13 @@ struct OzMaxSeg {
   int nd;
   int col_off;
   int stride;
+  int modulus;                   // 1: the modulus, 0: |Re| + |Im|
 };
 cudaError_t launch_oz_colmax(const OzMaxSeg* d_segs, int n_segs, int X, int sites_per_slab,
                              cudaStream_t s);
+// The diquark's row maxima (see ContractJob::oz_max) of every job of p.jobs; max_m_tiles:
+// the largest job's 128-row tiles
+cudaError_t launch_oz_rowmax(const ContractParams& p, int max_m_tiles, cudaStream_t s);
 // FP64 phases to double-float float4, n elements
 cudaError_t launch_phase_df(const double2* ph, float4* out, long long n, cudaStream_t s);
 cudaError_t launch_reduce_slabs(const ContractJob* d_jobs, int n_jobs, int n_slab, int P_total,

@@ -136,12 +136,17 @@ __device__ __forceinline__ int ceil_log2(float y) {
   return min(120, max(-120, e));
 }
 __device__ __forceinline__ float pow2(int e) { return __int_as_float((127 + e) << 23); }
-// row exponent of the diquark (u, v: line-1 and line-2 column maxima) and column exponent
-// of the third quark (w); the same arithmetic in the producers and the epilogue
-__device__ __forceinline__ int exp_a(float u, float v) {
-  return ceil_log2(__fmul_rn(__fmul_rn(2.f * u, v), 1.f + 0x1p-20f));
+// Row exponent of the diquark: M = the row's largest |Re D|, |Im D| computed in FP32 from the
+// fields' high parts (k_oz_rowmax), u, v = the line-1 and line-2 column maxima of |.|_1. The
+// FP32 evaluation and the double-float low parts move |Re D|, |Im D| by less than
+// 2^-21 (|u_b||v_c| + |u_c||v_b|) <= 2^-20 u v, so 2^eA >= (M + 2^-19 u v)(1 + 2^-20) bounds
+// every entry. Column exponent of the third quark: w = the largest |q3| (FP32 modulus of the
+// high parts, within 2^-22 of the exact modulus; |e^{-ip.x}| = 1), 2^eB >= w (1 + 2^-18).
+// The same arithmetic runs in the producers and the epilogue.
+__device__ __forceinline__ int exp_a(float M, float u, float v) {
+  return ceil_log2(__fmul_rn(__fmaf_rn(0x1p-19f * u, v, M), 1.f + 0x1p-20f));
 }
-__device__ __forceinline__ int exp_b(float w) { return ceil_log2(__fmul_rn(w, 1.f + 0x1p-20f)); }
+__device__ __forceinline__ int exp_b(float w) { return ceil_log2(__fmul_rn(w, 1.f + 0x1p-18f)); }
 
 // acc = a * b (double-float, three leading partial products)
 __device__ __forceinline__ dfloat df_prod(dfloat a, dfloat b) {
@@ -272,7 +277,10 @@ __device__ __forceinline__ void oz_produce(const ContractParams& prm, const OzSh
     const ContractJob& J = prm.jobs[w.job];
     const int nd1 = J.nd1, nd2 = J.nd2, nd3 = J.nd3;
     const int stride = nd1 + nd2 + nd3;
-    const float* mx = J.oz_max + (size_t)(w.slab < prm.n_slab ? w.slab : 0) * stride;
+    const int slab = w.slab < prm.n_slab ? w.slab : 0;
+    const float* mx = J.oz_max + (size_t)slab * stride;
+    // the slab's row maxima follow every slab's column maxima
+    const float* rmx = J.oz_max + (size_t)prm.n_slab * stride + (size_t)slab * nd1 * nd2;
     bool row_ok;
     int o1 = 0, o2 = 0, s1 = 0, s2 = 0, p = 0;
     float sc = 1.f;
@@ -281,7 +289,7 @@ __device__ __forceinline__ void oz_produce(const ContractParams& prm, const OzSh
       row_ok = row_used && m < nd1 * nd2;
       const int d1 = row_ok ? m / nd2 : 0, d2 = row_ok ? m - d1 * nd2 : 0;
       o1 = d1; o2 = d2; s1 = nd1; s2 = nd2;
-      if (row_ok) sc = pow2(-exp_a(mx[d1], mx[nd1 + d2]));
+      if (row_ok) sc = pow2(-exp_a(rmx[m], mx[d1], mx[nd1 + d2]));
     } else {
       const int n = (w.nt * C + (int)rank) * NC + rr;
       row_ok = row_used && n < prm.P * nd3;
@@ -598,11 +606,13 @@ k_contract_oz(const __grid_constant__ ContractParams prm) {
       const bool row_ok = m < M;
       const int n_base = (w.nt * C + (int)rank) * NC;
       const int stride = nd1 + nd2 + nd3;
-      const float* mx = J.oz_max + (size_t)(w.slab < prm.n_slab ? w.slab : 0) * stride;
+      const int slab = w.slab < prm.n_slab ? w.slab : 0;
+      const float* mx = J.oz_max + (size_t)slab * stride;
+      const float* rmx = J.oz_max + (size_t)prm.n_slab * stride + (size_t)slab * M;
       int eA = 0;
       if (row_ok) {
         const int d1 = m / nd2, d2 = m - d1 * nd2;
-        eA = exp_a(mx[d1], mx[nd1 + d2]);
+        eA = exp_a(rmx[m], mx[d1], mx[nd1 + d2]);
       }
       const int n_chunks = (w.n_stages + kChunk - 1) / kChunk;
       for (int ch = 0; ch < n_chunks; ++ch, ++c_g) {
@@ -717,12 +727,60 @@ __global__ void __launch_bounds__(256) k_oz_colmax(const OzMaxSeg* __restrict__ 
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float4 v = __ldg(g.field + ((size_t)x * 3 + c) * nd + d);
-      m = fmaxf(m, fabsf(v.x) + fabsf(v.z));
+      m = fmaxf(m, g.modulus ? sqrtf(fmaf(v.x, v.x, v.z * v.z)) : fabsf(v.x) + fabsf(v.z));
     }
   }
   if (slab >= 0)
     atomicMax(reinterpret_cast<unsigned int*>(g.out + (size_t)slab * g.stride + g.col_off + d),
               __float_as_uint(m));
+}
+
+// Row maxima of the diquark per site slab: for row m = (d1, d2), the largest |Re D_c| or
+// |Im D_c| over the slab's sites, spin pairs and colours, D evaluated in FP32 from the
+// fields' high parts. Block (site chunk, job x M tile), thread = row; one atomicMax per row
+// and slab a chunk touches (the maxima are zeroed before).
+constexpr int kRowmaxSites = 32;
+__global__ void __launch_bounds__(128) k_oz_rowmax(const __grid_constant__ ContractParams prm,
+                                                    int max_m_tiles) {
+  const int job = blockIdx.y / max_m_tiles, mt = blockIdx.y % max_m_tiles;
+  const ContractJob& J = prm.jobs[job];
+  const int M = J.nd1 * J.nd2;
+  const int m = mt * kOzM + threadIdx.x;
+  if (mt * kOzM >= M || m >= M) return;
+  const int nd1 = J.nd1, nd2 = J.nd2, d1 = m / nd2, d2 = m - d1 * nd2;
+  const int x0 = blockIdx.x * kRowmaxSites, x1 = min(prm.X, x0 + kRowmaxSites);
+  float* rmx = J.oz_max + (size_t)prm.n_slab * (nd1 + nd2 + J.nd3);
+  float mxv = 0.f;
+  int slab = -1;
+  for (int x = x0; x < x1; ++x) {
+    const int s = x / prm.sites_per_slab;
+    if (s != slab) {
+      if (slab >= 0)
+        atomicMax(reinterpret_cast<unsigned int*>(rmx + (size_t)slab * M + m), __float_as_uint(mxv));
+      slab = s;
+      mxv = 0.f;
+    }
+    for (int pr = 0; pr < prm.n_pairs; ++pr) {
+      const float4* uq = reinterpret_cast<const float4*>(J.q1[prm.a_slot[pr]]) + (size_t)x * 3 * nd1 + d1;
+      const float4* vq = reinterpret_cast<const float4*>(J.q2[prm.b_slot[pr]]) + (size_t)x * 3 * nd2 + d2;
+      float2 u[3], v[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4 a = __ldg(uq + (size_t)c * nd1), b = __ldg(vq + (size_t)c * nd2);
+        u[c] = make_float2(a.x, a.z);
+        v[c] = make_float2(b.x, b.z);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+        const float re = u[c1].x * v[c2].x - u[c1].y * v[c2].y - (u[c2].x * v[c1].x - u[c2].y * v[c1].y);
+        const float im = u[c1].x * v[c2].y + u[c1].y * v[c2].x - (u[c2].x * v[c1].y + u[c2].y * v[c1].x);
+        mxv = fmaxf(mxv, fmaxf(fabsf(re), fabsf(im)));
+      }
+    }
+  }
+  if (slab >= 0)
+    atomicMax(reinterpret_cast<unsigned int*>(rmx + (size_t)slab * M + m), __float_as_uint(mxv));
 }
 
 __global__ void k_phase_df(const double2* __restrict__ ph, float4* __restrict__ out, long long n) {
@@ -790,6 +848,13 @@ cudaError_t launch_oz_colmax(const OzMaxSeg* d_segs, int n_segs, int X, int site
   if (n_segs == 0) return cudaSuccess;
   dim3 grid((unsigned)((X + kColmaxSites - 1) / kColmaxSites), (unsigned)n_segs);
   k_oz_colmax<<<grid, 256, 0, s>>>(d_segs, X, sites_per_slab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_rowmax(const ContractParams& prm, int max_m_tiles, cudaStream_t s) {
+  if (prm.n_jobs == 0 || max_m_tiles == 0) return cudaSuccess;
+  dim3 grid((unsigned)((prm.X + kRowmaxSites - 1) / kRowmaxSites), (unsigned)(prm.n_jobs * max_m_tiles));
+  k_oz_rowmax<<<grid, 128, 0, s>>>(prm, max_m_tiles);
   return cudaGetLastError();
 }
 
