@@ -12,6 +12,8 @@ synthetic draws (``workloads.py``) resident on the device.
 The same line reports, on the same inputs:
 * the plain FP64 form, timed per dilution size on one job each and extrapolated to the
   batch's job mix (``fp64_form``), and the headline form's speedup over it;
+* the other FP64-accurate forms the same way (``fp64_accurate_forms``): double-float on the
+  FP32 pipe and the Ozaki digit-product form on the tensor cores;
 * per-block relative Frobenius errors of both against the CPU FP64 oracle on sampled
   entries of jobs taken from every wave (``oracle_check``);
 * the tile autotuner with and without its learned cost model (``tuning``);
@@ -85,6 +87,8 @@ FORMS = {
     "tf32x3": ("tf32x3", 6, 3, TF32_PEAK_TFLOPS, 1e-6),
     "bf16x3": ("bf16", 3, 3, BF16_PEAK_TFLOPS, 1e-4),
     "fp16x3": ("fp16x3", 6, 3, BF16_PEAK_TFLOPS, 1e-6),
+    # FP64-accurate on the BF16 tensor cores: 28 digit products of the folded complex GEMM
+    "ozaki": ("ozaki", 6, 28, BF16_PEAK_TFLOPS, 1e-12),
 }
 BATCH_HEAD = "fp16x3"
 
@@ -478,7 +482,8 @@ def tensor_roofline(form, prof, gemm_flops, alg_flops, steps, traffic, traffic_r
     sec = msc / 1e3
     alg = alg_flops * steps / sec / 1e12
     execd = gemm_flops * nprod * steps / sec / 1e12
-    return {"bound": "tensor", "kernel": "k_contract_tc", "path": path,
+    return {"bound": "tensor", "kernel": "k_contract_oz" if form == "ozaki" else "k_contract_tc",
+            "path": path,
             "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
             "flops": "algorithmic: Eq. 1 in the paper's ordering, 42 Pi D1D2 X + (24 Pi + 8 P) "
                      "D1D2D3 X per job (cmul 6, complex FMA 8)",
@@ -490,7 +495,8 @@ def tensor_roofline(form, prof, gemm_flops, alg_flops, steps, traffic, traffic_r
             "gemm_tflops": gemm_flops * steps / sec / 1e12,
             "gemm_frac": gemm_flops * steps / sec / 1e12 / peak,
             "executed_tflops": execd, "executed_frac": execd / peak,
-            "executed": "MMA piece products: the path's complex GEMM x %d" % nprod,
+            "executed": ("MMA digit products: the path's complex GEMM x %d" if form == "ozaki"
+                         else "MMA piece products: the path's complex GEMM x %d") % nprod,
             "launches": nc, "avg_launch_ms": msc / nc}
 
 
@@ -595,9 +601,21 @@ def run_batched(args, R, w, rank, local, clk):
     # of the first noise triple drawn with that size), timed with graph replays, then
     # extrapolated to the batch's job mix
     fp64 = None
+    accurate = {}
     if not args.no_fp64_form:
         fp64 = fp64_form_per_size(R, w, inp, V, phis, ms / args.steps, blocks_per_step,
                                   rank == 0 and not args.no_check)
+        # the other FP64-accurate forms (parity 1e-12) the same way: double-float on the FP32
+        # pipe, and the Ozaki digit-product form on the tensor cores
+        for name in ("df64", "ozaki"):
+            r = fp64_form_per_size(R, w, inp, V, phis, ms / args.steps, blocks_per_step,
+                                   rank == 0 and not args.no_check, form=name)
+            r["speedup_vs_fp64_form"] = fp64["extrapolated_ms_per_step"] / r["extrapolated_ms_per_step"]
+            accurate[name] = r
+        if accurate:
+            accurate["ozaki"]["speedup_vs_df64_form"] = (
+                accurate["df64"]["extrapolated_ms_per_step"]
+                / accurate["ozaki"]["extrapolated_ms_per_step"])
 
     # ---- the other mixed forms on a subset of the batch (the first 8 time slices of every
     # noise triple: 48 jobs), default tiles, graph-replayed; the headline form is timed on
@@ -644,6 +662,7 @@ def run_batched(args, R, w, rank, local, clk):
         "fp64_form": fp64,
         "speedup_vs_fp64_form": (fp64["extrapolated_ms_per_step"] / (ms / args.steps)
                                  if fp64 else None),
+        "fp64_accurate_forms": accurate or None,
         "tuning": tuning,
         "forms": forms,
         "e2e": e2e,
@@ -765,10 +784,12 @@ def tune_batched(R, w, inp, V, phis, ctx, head):
     }
 
 
-def fp64_form_per_size(R, w, inp, V, phis, head_ms_per_step, blocks_per_step, check):
-    """The plain FP64 form on one job per dilution size of the batch (graph-replayed, 3
-    warm-up + 2 timed calls each); the batch's FP64 time is the sum over its jobs of the
-    time of a job of that size."""
+def fp64_form_per_size(R, w, inp, V, phis, head_ms_per_step, blocks_per_step, check,
+                       form="fp64"):
+    """An FP64-accurate form (the plain FP64 form, double-float or the Ozaki tensor-core
+    form) on one job per dilution size of the batch (graph-replayed, 3 warm-up + 2 timed
+    calls each); the batch's time in that form is the sum over its jobs of the time of a
+    job of that size."""
     torch, bb, dev = R.torch, R.bb, R.dev
     n_t = inp.V.shape[0]
     P = len(inp.momenta)
@@ -778,7 +799,7 @@ def fp64_form_per_size(R, w, inp, V, phis, head_ms_per_step, blocks_per_step, ch
         nd = inp.ndil[k]
         if nd[0] in per_size:
             continue
-        c = R.context(w, "fp64", max(nd))
+        c = R.context(w, form, max(nd))
         B = torch.empty((1, P, *nd), dtype=torch.complex128, device=dev)
         jobs = [(V[0], phis[k][0][0], phis[k][1][0], phis[k][2][0], B[0])]
 
@@ -788,9 +809,17 @@ def fp64_form_per_size(R, w, inp, V, phis, head_ms_per_step, blocks_per_step, ch
         t_ms, pr, nl = R.measure(c, step, 2, 3)
         n_alpha, n_beta, pairs = spin_structure(inp.spins)
         alg = contraction_flops(w.X, nd, P, pairs)
+        if form == "fp64":
+            roof = fp64_roofline(pr, alg, 2, None, None)
+        elif form == "df64":
+            roof = df_roofline(pr, contraction_df_inst(w.X, nd, P, pairs), alg, 2)
+        else:
+            roof = tensor_roofline(form, pr, folded_gemm_flops(w.X, nd, P, pairs), alg, 2,
+                                   None, None, bb.bblock_last_path(c))
         per_size[nd[0]] = {"noise": k, "ms_per_job": t_ms / 2, "blocks_per_s": 2 * P / (t_ms / 1e3),
-                           "roofline": fp64_roofline(pr, alg, 2, None, None),
-                           "kernels": kernel_table(pr, t_ms)}
+                           "roofline": roof, "kernels": kernel_table(pr, t_ms)}
+        if form == "ozaki":
+            per_size[nd[0]]["cluster"] = bb.bblock_get_option(c, "tc_cluster")
         if check:
             full = [None] * w.n_noise
             full[k] = B.cpu()
@@ -811,12 +840,12 @@ def fp64_form_per_size(R, w, inp, V, phis, head_ms_per_step, blocks_per_step, ch
     if check:
         errs = []
         for k in picks:
-            r = oracle_check(inp, outs_chk[k], [(k, 0)], FORMS["fp64"][4])
+            r = oracle_check(inp, outs_chk[k], [(k, 0)], FORMS[form][4])
             errs.append(r)
         res["oracle_check"] = {"blocks_checked": sum(r["blocks_checked"] for r in errs),
                                "max": max(r["max"] for r in errs),
                                "median": statistics.median([r["median"] for r in errs]),
-                               "tolerance": FORMS["fp64"][4],
+                               "tolerance": FORMS[form][4],
                                "pass": all(r["pass"] for r in errs)}
     return res
 
@@ -965,7 +994,7 @@ def run_single(args, R, w, rank, head, clk, steps, warmup, extras=True):
         dt = max_over_ranks(time.perf_counter() - t0, R.world, dev)
         # the host path computes in chunks of time slices, whose site slabs may differ from
         # the device call's: the two agree to the form's rounding, not bit for bit
-        tol = 1e-12 if head in ("fp64", "df64") else 1e-5
+        tol = 1e-12 if head in ("fp64", "df64", "ozaki") else 1e-5
         ref = B.cpu().numpy()
         err = np.linalg.norm(hB.numpy() - ref) / max(np.linalg.norm(ref), 1e-300)
         assert err <= tol, f"host and device paths differ by {err:.2e}"
