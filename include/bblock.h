@@ -268,11 +268,16 @@ int bblock_last_wave_count(const bblock_ctx* ctx);
                                   BBLOCK_OPT_TC_NC sets the d3 columns per tile. Not with
                                   index checks, per-momentum coefficients or the wait-limit
                                   test hook */
-#define BBLOCK_OPT_TC_PROJECTION 12  /* mixed forms: 1 runs the projection (Eq. 2) on the
-                                       tensor cores in the form's operand split, accumulated as
-                                       in the contraction; 0 (default): FP32 FMA, which is
-                                       faster at the benchmarked sizes and more accurate. The
-                                       index checks use the FP32 projection */
+#define BBLOCK_OPT_TC_PROJECTION 12  /* mixed forms' projection (Eq. 2): 0 (default) on the
+                                       tensor cores from pre-tiled operands (V once per
+                                       distinct V of a call's wave, and every field's folded
+                                       phi, split into three BF16 pieces exact for FP32 and
+                                       written in the MMA's layout; staged by bulk copies;
+                                       six piece products, the leading one over four
+                                       accumulators): as accurate as FP32 FMA and faster;
+                                       1: on the tensor cores with operands built per stage in
+                                       the form's own split (the FP16 form then uses 2);
+                                       2: FP32 FMA. The index checks use the FP32 projection */
 #define BBLOCK_OPT_HOST_CHUNKS 11  /* bblock_compute_host: chunks of time slices whose copies
                                        overlap the computation, 1..64 (0, the default: 8). With
                                        1 the blocks equal those of bblock_compute bit for bit;

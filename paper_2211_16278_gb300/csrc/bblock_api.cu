@@ -87,7 +87,9 @@ struct bblock_ctx {
   int opt_corrupt_canary = 0; // test hook: the next call overwrites its first canary once
   int opt_tc_cluster = 0;     // tensor-core cluster size: 0 automatic, 1 none, 2 / 4 / 8
   int opt_host_chunks = 0;    // bblock_compute_host chunks of time slices (0: kHostChunks)
-  int opt_tc_proj = 0;        // mixed forms: Eq. 2 on the tensor cores (1) or FP32 FMA (0)
+  // mixed forms' Eq. 2: tiled tensor-core projection (0), per-stage tensor-core projection
+  // (1), FP32 FMA (2)
+  int opt_tc_proj = 0;
   int opt_tc_rows = 0;        // FP16 form: row-factored phase 0 where it pays, 1 where it fits, 2 never
   long long cycles_per_us = 2070;
 };
@@ -605,8 +607,20 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
   const int rf_min_slabs = rp.on ? (n_rows + std::max(1, 256 / rf_cpr) - 1) / std::max(1, 256 / rf_cpr) : 1;
   // checks option: a canary after the converted inputs and every field and partial block
   const size_t canary_bytes = c->opt_checks ? (size_t)(sp.n1 + sp.n2 + n3_fields + 2) * kCanaryBytes : 0;
-  // FP32 copies of a job's inputs (V and the three phi_i), converted once per call
+  // the tiled tensor-core projection (the default): V and the folded phi as BF16 piece tiles,
+  // V once per distinct V of a wave
+  const bool tiled = !c->opt_checks && c->opt_tc_proj == 0;
+  auto phi_tile_bytes = [&](const JobIn& j) -> size_t {
+    return align_up(sp.n1 * tiled_phi_bytes(j.nd[0], tiled_ncp(j.nd[0]), n_ev) +
+                        sp.n2 * tiled_phi_bytes(j.nd[1], tiled_ncp(j.nd[1]), n_ev) +
+                        n3_fields * tiled_phi_bytes(j.nd[2], tiled_ncp(j.nd[2]), n_ev),
+                    256);
+  };
+  // FP32 copies of a job's inputs (V and the three phi_i), converted once per call; tiled:
+  // the fields' phi tiles (the V tiles, one set per distinct V, precede the jobs)
+  const size_t v_tile_bytes = align_up(tiled_v_bytes(rows, n_ev), 256);
   auto in_bytes = [&](const JobIn& j) -> size_t {
+    if (tiled) return phi_tile_bytes(j);
     return align_up((size_t)rows * n_ev * sizeof(float2), 256) +
            align_up((size_t)4 * n_ev * (j.nd[0] + j.nd[1] + j.nd[2]) * sizeof(float2), 256);
   };
@@ -619,10 +633,14 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
   int rc;
   while (job_idx < jobs.size()) {
     size_t end = job_idx, need = 0;
+    std::vector<const double2*> wave_vs;   // tiled projection: the wave's distinct V
     while (end < jobs.size()) {
       size_t b = job_bytes(jobs[end], max_slabs);
+      const bool new_v = tiled && std::find(wave_vs.begin(), wave_vs.end(), jobs[end].V) == wave_vs.end();
+      if (new_v) b += v_tile_bytes;
       if (end > job_idx && need + b > wave_budget(c)) break;
       need += b;
+      if (new_v) wave_vs.push_back(jobs[end].V);
       ++end;
     }
     ++c->last_waves;
@@ -678,7 +696,8 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     // FP16 form: three per-line maxima per job (the operand scales), at the wave's start
     const bool amax_on = tc_form_needs_amax(form);
     const size_t amax_bytes = amax_on ? align_up((size_t)3 * nj * sizeof(uint32_t), 256) : 0;
-    size_t ws_need = amax_bytes;
+    const size_t vt_bytes = wave_vs.size() * v_tile_bytes;
+    size_t ws_need = amax_bytes + vt_bytes;
     for (size_t k = job_idx; k < end; ++k) ws_need += job_bytes(jobs[k], n_slab);
     rc = grow_device(c, &c->d_ws, &c->ws_cap, ws_need);
     if (rc) return rc;
@@ -689,8 +708,15 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     std::vector<uint32_t*> canaries;
     std::vector<F32ConvSeg> segs;
     long long max_seg = 0;
-    char* ws = c->d_ws + amax_bytes;
+    char* ws = c->d_ws + amax_bytes + vt_bytes;
     long long unit = 0;
+    // tiled projection: the distinct V of the wave (tiles after the maxima) and every field's
+    // phi tiles
+    std::vector<TileV> tvs;
+    for (size_t q = 0; q < wave_vs.size(); ++q)
+      tvs.push_back(TileV{wave_vs[q], reinterpret_cast<uint16_t*>(c->d_ws + amax_bytes + q * v_tile_bytes)});
+    std::vector<TiledField> tfields;
+    std::vector<int> tfield_v;
     for (int k = 0; k < nj; ++k) {
       const JobIn& j = jobs[job_idx + k];
       char* base = ws;
@@ -699,18 +725,28 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
         canaries.push_back(reinterpret_cast<uint32_t*>(at));
         at += kCanaryBytes;
       };
-      // the job's inputs in FP32: V, then phi_1..3 packed
-      const float2* Vf = reinterpret_cast<const float2*>(base);
-      segs.push_back(F32ConvSeg{j.V, reinterpret_cast<float2*>(base), (long long)rows * n_ev});
-      max_seg = std::max(max_seg, (long long)rows * n_ev);
-      char* pb = base + align_up((size_t)rows * n_ev * sizeof(float2), 256);
-      const float2* phif[3];
-      for (int i = 0; i < 3; ++i) {
-        phif[i] = reinterpret_cast<const float2*>(pb);
-        const long long n = 4LL * n_ev * j.nd[i];
-        segs.push_back(F32ConvSeg{j.phi[i], reinterpret_cast<float2*>(pb), n});
-        max_seg = std::max(max_seg, n);
-        pb += (size_t)n * sizeof(float2);
+      const float2* Vf = nullptr;
+      const float2* phif[3] = {};
+      char* phi_tiles = nullptr;
+      int vidx = -1;
+      if (tiled) {
+        for (size_t q = 0; q < tvs.size(); ++q)
+          if (tvs[q].V == j.V) vidx = (int)q;
+        if (vidx < 0) return fail(c, BBLOCK_ERR_INVALID_ARG, "internal: V of a job not in its wave");
+        phi_tiles = base;
+      } else {
+        // the job's inputs in FP32: V, then phi_1..3 packed
+        Vf = reinterpret_cast<const float2*>(base);
+        segs.push_back(F32ConvSeg{j.V, reinterpret_cast<float2*>(base), (long long)rows * n_ev});
+        max_seg = std::max(max_seg, (long long)rows * n_ev);
+        char* pb = base + align_up((size_t)rows * n_ev * sizeof(float2), 256);
+        for (int i = 0; i < 3; ++i) {
+          phif[i] = reinterpret_cast<const float2*>(pb);
+          const long long n = 4LL * n_ev * j.nd[i];
+          segs.push_back(F32ConvSeg{j.phi[i], reinterpret_cast<float2*>(pb), n});
+          max_seg = std::max(max_seg, n);
+          pb += (size_t)n * sizeof(float2);
+        }
       }
       base += in_bytes(j);
       canary(base);
@@ -724,6 +760,21 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
         f.nd = nd;
         f.n_terms = n_terms;
         for (int t = 0; t < n_terms; ++t) { f.row_off[t] = offs[t]; f.w[t] = w[t]; }
+        if (tiled) {
+          TiledField tf{};
+          tf.phi = j.phi[line];
+          for (int t = 0; t < n_terms; ++t) { tf.row_off[t] = offs[t]; tf.w[t] = w[t]; }
+          tf.n_terms = n_terms;
+          tf.nd = nd;
+          tf.ncp = tiled_ncp(nd);
+          tf.n_tiles = (nd + tf.ncp - 1) / tf.ncp;
+          tf.btiles = reinterpret_cast<uint16_t*>(phi_tiles);
+          phi_tiles += tiled_phi_bytes(nd, tf.ncp, n_ev);
+          tf.q = f.q;
+          tf.amax = f.amax;
+          tfields.push_back(tf);
+          tfield_v.push_back(vidx);
+        }
         base += (size_t)rows * nd * sizeof(float2);
         canary(base);
         fields.push_back(f);
@@ -794,7 +845,43 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
     const size_t cofs = sofs + align_up(segs.size() * sizeof(F32ConvSeg), 256);
     // row-factored: w^k = e^{-2 pi i k / L}, k = 0..L-1, in FP64 rounded to FP32
     const size_t wofs = align_up(cofs + canaries.size() * sizeof(uint32_t*), 256);
-    std::vector<char> tab(wofs + (rp.on ? (size_t)L * sizeof(float2) : 0));
+    // tiled projection: the field tiles grouped by V (units: 128-row tile outermost within a
+    // group, so the CTAs running at once share their V tiles in L2)
+    std::vector<FieldTile> tfts;
+    std::vector<PGroup> tgroups;
+    TiledProjParams tpp{};
+    if (tiled) {
+      tpp.rows = rows;
+      tpp.n_ev = n_ev;
+      tpp.k_stages = (n_ev + 31) / 32;
+      tpp.m_tiles = (rows + 127) / 128;
+      long long ub = 0;
+      for (int v = 0; v < (int)tvs.size(); ++v) {
+        PGroup g{ub, (int)tfts.size(), 0, v};
+        for (size_t f = 0; f < tfields.size(); ++f)
+          if (tfield_v[f] == v)
+            for (int nt = 0; nt < tfields[f].n_tiles; ++nt) tfts.push_back(FieldTile{(int)f, nt});
+        g.ft_count = (int)tfts.size() - g.ft_first;
+        if (g.ft_count == 0) continue;
+        ub += (long long)tpp.m_tiles * g.ft_count;
+        tgroups.push_back(g);
+      }
+      tpp.n_groups = (int)tgroups.size();
+      tpp.total_units = ub;
+    }
+    const size_t tofs = align_up(wofs + (rp.on ? (size_t)L * sizeof(float2) : 0), 256);
+    const size_t tv_ofs = tofs;
+    const size_t tf_ofs = align_up(tv_ofs + tvs.size() * sizeof(TileV), 256);
+    const size_t tft_ofs = align_up(tf_ofs + tfields.size() * sizeof(TiledField), 256);
+    const size_t tg_ofs = align_up(tft_ofs + tfts.size() * sizeof(FieldTile), 256);
+    std::vector<char> tab(tiled ? tg_ofs + tgroups.size() * sizeof(PGroup)
+                                : wofs + (rp.on ? (size_t)L * sizeof(float2) : 0));
+    if (tiled) {
+      memcpy(tab.data() + tv_ofs, tvs.data(), tvs.size() * sizeof(TileV));
+      memcpy(tab.data() + tf_ofs, tfields.data(), tfields.size() * sizeof(TiledField));
+      memcpy(tab.data() + tft_ofs, tfts.data(), tfts.size() * sizeof(FieldTile));
+      memcpy(tab.data() + tg_ofs, tgroups.data(), tgroups.size() * sizeof(PGroup));
+    }
     if (rp.on) {
       float2* om = reinterpret_cast<float2*>(tab.data() + wofs);
       const double two_pi = 6.283185307179586476925286766559;
@@ -819,13 +906,30 @@ int run_jobs_tc(bblock_ctx* c, const std::vector<JobIn>& jobs, const SpinPlan& s
         CK(c, cudaMemsetAsync(canaries[0], 0x5a, 4, s));
       }
     }
-    CK(c, timed_launch(c, K_CONVERT, s, [&] {
-      return launch_convert_f32(reinterpret_cast<const F32ConvSeg*>(c->d_tab + sofs),
-                                (int)segs.size(), max_seg, s);
-    }));
+    if (!tiled)
+      CK(c, timed_launch(c, K_CONVERT, s, [&] {
+        return launch_convert_f32(reinterpret_cast<const F32ConvSeg*>(c->d_tab + sofs),
+                                  (int)segs.size(), max_seg, s);
+      }));
     if (amax_on) CK(c, cudaMemsetAsync(d_amax, 0, (size_t)3 * nj * sizeof(uint32_t), s));
-    // the FP16 form takes its operand scales from the FP32 projection's field maxima
-    if (c->opt_checks || !c->opt_tc_proj || amax_on) {
+    if (tiled) {
+      // Eq. 2 on the tensor cores from pre-tiled BF16 pieces (it also writes the FP16 form's
+      // field maxima)
+      tpp.vs = reinterpret_cast<const TileV*>(c->d_tab + tv_ofs);
+      tpp.fields = reinterpret_cast<const TiledField*>(c->d_tab + tf_ofs);
+      tpp.fts = reinterpret_cast<const FieldTile*>(c->d_tab + tft_ofs);
+      tpp.groups = reinterpret_cast<const PGroup*>(c->d_tab + tg_ofs);
+      tpp.status = c->d_status;
+      tpp.wait_limit = c->opt_wait_us > 0 ? (long long)c->opt_wait_us * c->cycles_per_us
+                                          : 4000000000LL;
+      const int pgrid = (int)std::min<long long>(tpp.total_units, c->num_sms);
+      CK(c, timed_launch(c, K_PROJECT, s, [&] {
+        return launch_project_tiled(tpp, (int)tvs.size(), (int)tfts.size(), pgrid, s);
+      }));
+    } else if (c->opt_checks || c->opt_tc_proj == 2 || amax_on) {
+      // the FP32 projection: the checked variant (it checks every index), on request, and for
+      // the FP16 form when the per-stage projection is asked for (it takes its operand scales
+      // from the FP32 projection's field maxima)
       // the FP32 projection (the default, and the checked variant: it checks every index)
       CK(c, timed_launch(c, K_PROJECT, s, [&] {
         return launch_project_f32(d_fields, (int)fields.size(), rows, n_ev, max_ndf,
@@ -2082,7 +2186,7 @@ int bblock_set_option(bblock_ctx* c, int option, int value) {
       drop_graph(c);
       return BBLOCK_OK;
     case BBLOCK_OPT_TC_PROJECTION:
-      if (value != 0 && value != 1) break;
+      if (value < 0 || value > 2) break;
       c->opt_tc_proj = value;
       return BBLOCK_OK;
     case BBLOCK_OPT_HOST_CHUNKS:

@@ -258,6 +258,54 @@ cudaError_t launch_project_df(const ProjField* d_fields, int n_fields, int rows,
                               int max_nd, cudaStream_t s);
 int fp64_contract_ctas_per_sm(int P, int rn, int n_pairs);
 
+// ---------------------------------------------------------------- tiled tensor-core projection
+
+// Eq. 2 for the mixed forms with pre-tiled BF16 piece operands (proj_tiled.cu).
+constexpr int kTiledMaxNC = 48;   // widest N tile (complex columns)
+struct TileV {                    // one distinct V of a wave
+  const double2* V;               // [n_ev][rows] FP64 (the caller's buffer)
+  uint16_t* tiles;                // [m_tiles][k_stages] 48 KB blocks of A pieces
+};
+struct TiledField {               // one field q of Eq. 2
+  const double2* phi;             // [4 n_ev][nd] FP64 (the caller's buffer)
+  double2 w[kMaxTerms];           // folded coefficients, rows row_off[t] + l
+  int row_off[kMaxTerms];
+  int n_terms;
+  int nd, ncp, n_tiles;           // columns, N tile width (16..64), N tiles
+  uint16_t* btiles;               // [n_tiles][k_stages] blocks of B pieces (9 ncp 64 bytes)
+  float2* q;                      // [rows][nd] FP32 output
+  uint32_t* amax;                 // FP16 form: the quark line's largest |Re| or |Im| (or null)
+};
+struct FieldTile { int field, nt; };
+struct PGroup {                   // the field tiles of one V: units (128-row tile, field tile)
+  long long unit_begin;
+  int ft_first, ft_count, vidx;
+};
+struct TiledProjParams {
+  const TileV* vs;
+  const TiledField* fields;
+  const FieldTile* fts;
+  const PGroup* groups;
+  int n_groups;
+  long long total_units;
+  int rows, n_ev, k_stages, m_tiles;
+  int* status;
+  long long wait_limit;
+};
+cudaError_t launch_project_tiled(const TiledProjParams& p, int n_vs, int n_fts, int grid,
+                                 cudaStream_t s);
+size_t tiled_v_bytes(int rows, int n_ev);
+size_t tiled_phi_bytes(int nd, int ncp, int n_ev);
+// the N tile (16, 32 or 48 columns) with the fewest padded columns, the wider on a tie
+inline int tiled_ncp(int nd) {
+  int best = 48, pad = 1 << 30;
+  for (int nc = 48; nc >= 16; nc -= 16) {
+    const int p = (nd + nc - 1) / nc * nc - nd;
+    if (p < pad) { pad = p; best = nc; }
+  }
+  return best;
+}
+
 // ---------------------------------------------------------------- Ozaki form
 
 // FP64-accurate contraction on the BF16 tensor cores (oz_contract.cu): units (job, 128-row

@@ -142,6 +142,15 @@ __device__ __forceinline__ void copy_to_peer(uint32_t dst_cluster, uint32_t src,
       "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
       ::"r"(dst_cluster), "r"(src), "r"(bytes), "r"(mbar_cluster) : "memory");
 }
+// bulk copy of `bytes` from global memory into this CTA's shared memory; completion is
+// counted as transaction bytes on the mbarrier (both addresses 16-byte aligned, bytes a
+// multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void* src, uint32_t bytes,
+                                         uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst_smem), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t a, uint32_t tx) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(tx)
                : "memory");

@@ -116,7 +116,7 @@ def test_graph_replay_and_switching_the_projection(env):
         outs.append(B.cpu().numpy())
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
-    bb.bblock_set_option(ctx, "tc_projection", 0)
+    bb.bblock_set_option(ctx, "tc_projection", 2)
     bb.bblock_compute(ctx, V, *phis, mom, spins, coeffs, B_out=B, stream=stream)
     bb.bblock_status(ctx)
     fp32 = B.cpu().numpy()
@@ -124,5 +124,5 @@ def test_graph_replay_and_switching_the_projection(env):
     ref = reference(inp)
     assert rel(fp32, ref) <= 1e-6 and rel(outs[0], ref) <= 1e-6
     with pytest.raises(bb.BblockError):
-        bb.bblock_set_option(ctx, "tc_projection", 2)
+        bb.bblock_set_option(ctx, "tc_projection", 3)
     bb.bblock_destroy(ctx)
