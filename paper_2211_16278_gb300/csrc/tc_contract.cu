@@ -475,6 +475,12 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
     }
     const int NG = is_a ? R::kAGroups : R::kBGroups;
     const bool row_used = is_a || (is_b && b_row_in);
+    // row-factored: a stage's first group (site x0 = xl of its lattice row, pair pr) and the
+    // phase index (n0 x0) mod L advance incrementally from stage to stage, with no division
+    // in the stage loop: each stage moves G groups on (G / np sites and G % np pairs)
+    const int rf_gq = RF ? G / prm.n_pairs : 0, rf_gr = RF ? G % prm.n_pairs : 0;
+    const int rf_xl0 = RF ? g0 / prm.n_pairs : 0, rf_pr0 = RF ? g0 % prm.n_pairs : 0;
+    int rf_sub = 0, rf_row = 0, rf_xl = 0, rf_pr = 0, rf_ph = 0, rf_ph0 = 0, rf_step = 0;
     long long s_g = 0;
     for (long long u = u0; u < prm.total_units; u += du) {
       const Unit w = decode(u);
@@ -547,6 +553,12 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
         __syncwarp();
         named_bar(kBarProd, R::kProdThreads);
         if constexpr (!RF) phase_p = prm.phase + (size_t)pidx * prm.X;
+        if constexpr (RF) {
+          rf_ph0 = (pidx * rf_xl0) % prm.L;
+          rf_step = (pidx * rf_gq) % prm.L;
+          rf_sub = 0; rf_row = 0;
+          rf_xl = rf_xl0; rf_pr = rf_pr0; rf_ph = rf_ph0;
+        }
       }
       for (int st = 0; st < w.n_stages; ++st, ++s_g) {
         const int slot = (int)(s_g % STAGES);
@@ -598,13 +610,16 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
           } else {
             // the stage's sites [sx0, sx1) and this thread's first group of its run of NG
             // (row-factored: the stage's row, groups counted from the row's first site)
-            int sx0 = w.x_begin, sx1 = w.x_end, gi0 = st * G + g0;
+            int sx0 = w.x_begin, sx1 = w.x_end, xl, pr, ph = 0;
             if constexpr (RF) {
-              sx0 = (w.x_begin + st / prm.rf_spr) * prm.L;
+              sx0 = (w.x_begin + rf_row) * prm.L;
               sx1 = sx0 + prm.L;
-              gi0 = (st % prm.rf_spr) * G + g0;
+              xl = rf_xl; pr = rf_pr; ph = rf_ph;
+            } else {
+              const int gi0 = st * G + g0;
+              xl = gi0 / np;
+              pr = gi0 - xl * np;
             }
-            int xl = gi0 / np, pr = gi0 - xl * np;
             uint32_t vmask = 0;   // groups of this run that lie inside the slab and a used row
 #pragma unroll
             for (int half = 0; half < 8 / kLoadRun; ++half) {
@@ -634,10 +649,17 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                 } else {
                   const float2* q = s_q3[pr] + (size_t)xs * 3 * s1 + off1;
                   ld[j][0] = q[0]; ld[j][1] = q[s1]; ld[j][2] = q[2 * s1];
-                  if constexpr (RF) ld[j][3] = s_omega[(pidx * (xs - sx0)) % prm.L];
+                  if constexpr (RF) ld[j][3] = s_omega[ph];
                   else ld[j][3] = phase_p[xs];
                 }
-                if (++pr == np) { pr = 0; ++xl; }
+                if (++pr == np) {
+                  pr = 0;
+                  ++xl;
+                  if constexpr (RF) {
+                    ph += pidx;
+                    if (ph >= prm.L) ph -= prm.L;
+                  }
+                }
               }
 #pragma unroll
               for (int j = 0; j < kLoadRun; ++j) {
@@ -769,6 +791,19 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
             mbar_arrive(smem_u32(&bar_full[slot]));
         }
         __syncwarp();
+        if constexpr (RF) {
+          // the next stage's first group: G groups on, or the next row's first
+          if (++rf_sub == prm.rf_spr) {
+            rf_sub = 0; ++rf_row;
+            rf_xl = rf_xl0; rf_pr = rf_pr0; rf_ph = rf_ph0;
+          } else {
+            rf_xl += rf_gq;
+            rf_pr += rf_gr;
+            rf_ph += rf_step;
+            if (rf_pr >= np) { rf_pr -= np; ++rf_xl; rf_ph += pidx; }
+            while (rf_ph >= prm.L) rf_ph -= prm.L;
+          }
+        }
       }
     }
   } else if (warp == kMmaWarp) {
