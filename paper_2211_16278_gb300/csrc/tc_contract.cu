@@ -43,6 +43,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "bblock_internal.h"
 #include "tc_ptx.cuh"
@@ -621,78 +622,87 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
               pr = gi0 - xl * np;
             }
             uint32_t vmask = 0;   // groups of this run that lie inside the slab and a used row
+            // One role's groups, with their group count and loads per group known at compile
+            // time, so that each role's load buffers take only its own registers: the
+            // diquark side loads 6 values per group in rounds of kLoadRun groups, the
+            // third-quark side 4 per group, all of its groups in one round (unchecked).
+            auto build = [&](auto kNG, auto kIsA) {
+              constexpr int NGc = decltype(kNG)::value;
+              constexpr bool Ac = decltype(kIsA)::value;
+              constexpr int LR = Ac ? (kLoadRun < NGc ? kLoadRun : NGc) : (CHECKS ? 4 : NGc);
+              constexpr int NV = Ac ? 6 : 4;
 #pragma unroll
-            for (int half = 0; half < 8 / kLoadRun; ++half) {
-              if (half * kLoadRun >= NG) break;
-              // kLoadRun groups: issue every load first, then compute
-              float2 ld[kLoadRun][6];
-              bool vld[kLoadRun];
+              for (int half = 0; half < NGc / LR; ++half) {
+                // LR groups: issue every load first, then compute
+                float2 ld[LR][NV];
+                bool vld[LR];
 #pragma unroll
-              for (int j = 0; j < kLoadRun; ++j) {
-                if (half * kLoadRun + j >= NG) break;
-                const int x = sx0 + xl;
-                vld[j] = row_ok && x < sx1;
-                int xs = vld[j] ? x : sx0;
-                if (CHECKS) {
-                  const long long fl = 3LL * prm.X * s1;            // elements of a field
-                  bool good = idx_ok(prm, (long long)xs * 3 * s1 + off1 + 2LL * s1, fl, is_a ? 1 : 3, w.job) &&
-                              idx_ok(prm, pr, np, 6, w.job);
-                  if (is_a) good = good && idx_ok(prm, (long long)xs * 3 * s2 + off2 + 2LL * s2, 3LL * prm.X * s2, 2, w.job);
-                  else good = good && idx_ok(prm, (long long)pidx * prm.X + xs, (long long)prm.P * prm.X, 4, w.job);
-                  if (!good) { vld[j] = false; xs = 0; pr = 0; }
-                }
-                if (is_a) {
-                  const float2* uq = s_q1[pr] + (size_t)xs * 3 * s1 + off1;
-                  const float2* vq = s_q2[pr] + (size_t)xs * 3 * s2 + off2;
-                  ld[j][0] = uq[0]; ld[j][1] = uq[s1]; ld[j][2] = uq[2 * s1];
-                  ld[j][3] = vq[0]; ld[j][4] = vq[s2]; ld[j][5] = vq[2 * s2];
-                } else {
-                  const float2* q = s_q3[pr] + (size_t)xs * 3 * s1 + off1;
-                  ld[j][0] = q[0]; ld[j][1] = q[s1]; ld[j][2] = q[2 * s1];
-                  if constexpr (RF) ld[j][3] = s_omega[ph];
-                  else ld[j][3] = phase_p[xs];
-                }
-                if (++pr == np) {
-                  pr = 0;
-                  ++xl;
-                  if constexpr (RF) {
-                    ph += pidx;
-                    if (ph >= prm.L) ph -= prm.L;
+                for (int j = 0; j < LR; ++j) {
+                  const int x = sx0 + xl;
+                  vld[j] = row_ok && x < sx1;
+                  int xs = vld[j] ? x : sx0;
+                  if (CHECKS) {
+                    const long long fl = 3LL * prm.X * s1;            // elements of a field
+                    bool good = idx_ok(prm, (long long)xs * 3 * s1 + off1 + 2LL * s1, fl, Ac ? 1 : 3, w.job) &&
+                                idx_ok(prm, pr, np, 6, w.job);
+                    if (Ac) good = good && idx_ok(prm, (long long)xs * 3 * s2 + off2 + 2LL * s2, 3LL * prm.X * s2, 2, w.job);
+                    else good = good && idx_ok(prm, (long long)pidx * prm.X + xs, (long long)prm.P * prm.X, 4, w.job);
+                    if (!good) { vld[j] = false; xs = 0; pr = 0; }
+                  }
+                  if constexpr (Ac) {
+                    const float2* uq = s_q1[pr] + (size_t)xs * 3 * s1 + off1;
+                    const float2* vq = s_q2[pr] + (size_t)xs * 3 * s2 + off2;
+                    ld[j][0] = uq[0]; ld[j][1] = uq[s1]; ld[j][2] = uq[2 * s1];
+                    ld[j][3] = vq[0]; ld[j][4] = vq[s2]; ld[j][5] = vq[2 * s2];
+                  } else {
+                    const float2* q = s_q3[pr] + (size_t)xs * 3 * s1 + off1;
+                    ld[j][0] = q[0]; ld[j][1] = q[s1]; ld[j][2] = q[2 * s1];
+                    if constexpr (RF) ld[j][3] = s_omega[ph];
+                    else ld[j][3] = phase_p[xs];
+                  }
+                  if (++pr == np) {
+                    pr = 0;
+                    ++xl;
+                    if constexpr (RF) {
+                      ph += pidx;
+                      if (ph >= prm.L) ph -= prm.L;
+                    }
                   }
                 }
-              }
 #pragma unroll
-              for (int j = 0; j < kLoadRun; ++j) {
-                if (half * kLoadRun + j >= NG) break;
-                float2 c0, c1, c2;
-                if (is_a) {
-                  const float2 u0 = ld[j][0], u1 = ld[j][1], u2 = ld[j][2];
-                  const float2 v0 = ld[j][3], v1 = ld[j][4], v2 = ld[j][5];
-                  const float2 a12 = cmulf(u1, v2), a21 = cmulf(u2, v1);
-                  const float2 a20 = cmulf(u2, v0), a02 = cmulf(u0, v2);
-                  const float2 a01 = cmulf(u0, v1), a10 = cmulf(u1, v0);
-                  c0 = make_float2(a12.x - a21.x, a12.y - a21.y);
-                  c1 = make_float2(a20.x - a02.x, a20.y - a02.y);
-                  c2 = make_float2(a01.x - a10.x, a01.y - a10.y);
-                  if constexpr (F16) {
-                    c0.x *= f16s; c0.y *= f16s;
-                    c1.x *= f16s; c1.y *= f16s;
-                    c2.x *= f16s; c2.y *= f16s;
+                for (int j = 0; j < LR; ++j) {
+                  float2 c0, c1, c2;
+                  if constexpr (Ac) {
+                    const float2 u0 = ld[j][0], u1 = ld[j][1], u2 = ld[j][2];
+                    const float2 v0 = ld[j][3], v1 = ld[j][4], v2 = ld[j][5];
+                    const float2 a12 = cmulf(u1, v2), a21 = cmulf(u2, v1);
+                    const float2 a20 = cmulf(u2, v0), a02 = cmulf(u0, v2);
+                    const float2 a01 = cmulf(u0, v1), a10 = cmulf(u1, v0);
+                    c0 = make_float2(a12.x - a21.x, a12.y - a21.y);
+                    c1 = make_float2(a20.x - a02.x, a20.y - a02.y);
+                    c2 = make_float2(a01.x - a10.x, a01.y - a10.y);
+                    if constexpr (F16) {
+                      c0.x *= f16s; c0.y *= f16s;
+                      c1.x *= f16s; c1.y *= f16s;
+                      c2.x *= f16s; c2.y *= f16s;
+                    }
+                  } else {
+                    float2 phv = ld[j][3];
+                    if constexpr (F16) { phv.x *= f16s; phv.y *= f16s; }
+                    c0 = cmulf(phv, ld[j][0]);
+                    c1 = cmulf(phv, ld[j][1]);
+                    c2 = cmulf(phv, ld[j][2]);
                   }
-                } else {
-                  float2 ph = ld[j][3];
-                  if constexpr (F16) { ph.x *= f16s; ph.y *= f16s; }
-                  c0 = cmulf(ph, ld[j][0]);
-                  c1 = cmulf(ph, ld[j][1]);
-                  c2 = cmulf(ph, ld[j][2]);
+                  const int jj = half * LR + j;
+                  vmask |= (uint32_t)vld[j] << jj;
+                  re[0][jj] = c0.x; im[0][jj] = c0.y;
+                  re[1][jj] = c1.x; im[1][jj] = c1.y;
+                  re[2][jj] = c2.x; im[2][jj] = c2.y;
                 }
-                const int jj = half * kLoadRun + j;
-                vmask |= (uint32_t)vld[j] << jj;
-                re[0][jj] = c0.x; im[0][jj] = c0.y;
-                re[1][jj] = c1.x; im[1][jj] = c1.y;
-                re[2][jj] = c2.x; im[2][jj] = c2.y;
               }
-            }
+            };
+            if (is_a) build(std::integral_constant<int, R::kAGroups>{}, std::true_type{});
+            else build(std::integral_constant<int, R::kBGroups>{}, std::false_type{});
             // groups past the slab's end or of an unused row (their loads read a valid site)
             // contribute zeros; this branch is taken only at ragged edges
             if (vmask != (1u << NG) - 1u) {
