@@ -388,6 +388,8 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   __shared__ const float2* s_q1[kMaxPairs];
   __shared__ const float2* s_q2[kMaxPairs];
   __shared__ const float2* s_q3[kMaxPairs];
+  // row-factored: the current lattice row's phase per momentum (epilogue)
+  __shared__ float2 s_rowph[kMaxRfP];
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int NC = prm.NC;
@@ -921,15 +923,26 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                             &abort_flag, prm.status, prm.wait_limit);
         // the TMEM loads below are warp-collective: decide per warp
         ok = __all_sync(0xffffffffu, ok);
+        if (RF && ch % cpr == 0) {
+          // row-factored, a new lattice row: its phase w^{n1 x1 + n2 x2} per momentum, once
+          // per row, into shared memory. Every epilogue warp takes this step (whether or not
+          // it drains), after the previous drain's barrier and before this row's reads.
+          const int lrow = w.x_begin + ch / cpr;
+          const int x1 = lrow % prm.L, x2 = lrow / prm.L;
+          if (row < prm.P)
+            s_rowph[row] = s_omega[(prm.rf_pn1[row] * x1 + prm.rf_pn2[row] * x2) % prm.L];
+          __syncwarp();
+          named_bar(kBarEpi, kEpiWarps * 32);
+        }
         if (ok && RF) {
           // row-factored: chunk sums t = lead + corr of each n0 block, times the row's
           // w^{n1 x1 + n2 x2}, into the running sum of every momentum with that n0
           tc_fence_after();
           const uint32_t lead = tmem + lane_base;
-          const int row = w.x_begin + ch / cpr;
-          const int x1 = row % prm.L, x2 = row / prm.L;
           const int ncol = prm.rf_nc;
           for (int i0 = 0; i0 < prm.rf_nidx; ++i0) {
+            uint32_t msk = 0;   // the momenta with this n0
+            for (int p = 0; p < prm.P; ++p) msk |= (prm.rf_pidx0[p] == i0 ? 1u : 0u) << p;
             for (int col = 0; col < ncol; col += 16) {
               float tr[16], ti[16], cr[16], ci[16];
               tmem_ld16(lead + i0 * ncol + col, tr);
@@ -944,9 +957,10 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                 tr[i] = r2.x; tr[i + 1] = r2.y;
                 ti[i] = i2.x; ti[i + 1] = i2.y;
               }
-              for (int p = 0; p < prm.P; ++p) {
-                if (prm.rf_pidx0[p] != i0) continue;
-                const float2 ph = s_omega[(prm.rf_pn1[p] * x1 + prm.rf_pn2[p] * x2) % prm.L];
+              // the momenta with this n0: run += ph x t, the row's phase from shared memory
+              for (uint32_t m2 = msk; m2 != 0u; m2 &= m2 - 1u) {
+                const int p = __ffs(m2) - 1;
+                const float2 ph = s_rowph[p];
                 const uint32_t rp = run_r + (uint32_t)(p * 2 * ncol + col);
                 float rr[16], ri[16];
                 if (ch > 0) {
@@ -954,7 +968,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                   tmem_ld16(rp + ncol, ri);
                   tmem_wait_ld();
                 }
-                // run += ph x t, two adjacent columns per packed FMA (each lane rounds as fmaf):
+                // two adjacent columns per packed FMA (each lane rounds as fmaf):
                 //   re = ph.x tr - ph.y ti + re,   im = ph.x ti + ph.y tr + im
                 const float2 phx = make_float2(ph.x, ph.x), phy = make_float2(ph.y, ph.y);
                 const float2 nphy = make_float2(-ph.y, -ph.y);
