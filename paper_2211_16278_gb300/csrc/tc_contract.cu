@@ -390,6 +390,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   __shared__ const float2* s_q3[kMaxPairs];
   // row-factored: the current lattice row's phase per momentum (epilogue)
   __shared__ float2 s_rowph[kMaxRfP];
+  __shared__ uint32_t s_rfmask[kMaxRfIdx];
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int NC = prm.NC;
@@ -417,6 +418,12 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   float2* s_omega = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);
   if constexpr (RF) {
     for (int k = tid; k < prm.L; k += blockDim.x) s_omega[k] = prm.rf_omega[k];
+    // the momenta of each distinct n0, as a bit mask
+    if (tid < prm.rf_nidx) {
+      uint32_t msk = 0;
+      for (int p = 0; p < prm.P; ++p) msk |= (prm.rf_pidx0[p] == tid ? 1u : 0u) << p;
+      s_rfmask[tid] = msk;
+    }
   }
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -941,8 +948,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
           const uint32_t lead = tmem + lane_base;
           const int ncol = prm.rf_nc;
           for (int i0 = 0; i0 < prm.rf_nidx; ++i0) {
-            uint32_t msk = 0;   // the momenta with this n0
-            for (int p = 0; p < prm.P; ++p) msk |= (prm.rf_pidx0[p] == i0 ? 1u : 0u) << p;
+            const uint32_t msk = s_rfmask[i0];   // the momenta with this n0
             for (int col = 0; col < ncol; col += 16) {
               float tr[16], ti[16], cr[16], ci[16];
               tmem_ld16(lead + i0 * ncol + col, tr);
