@@ -835,21 +835,25 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                              ((n_mma >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
       const uint32_t idesc_neg = idesc | (1u << 14);
       long long s_g = 0, c_g = 0;
+      // the chunk's accumulator buffer (c_g mod nbuf) and the parity of its use (c_g / nbuf),
+      // kept incrementally: no division on the MMA thread's path between stages
+      int buf = 0;
+      uint32_t buf_par = 0;
       bool stop = false;
       for (long long u = u0; u < prm.total_units && !stop; u += du) {
         const Unit w = decode(u);
         // chunks of chunk_stages stages; row-factored: no chunk crosses a lattice row
         const int spr = RF ? prm.rf_spr : w.n_stages;
+        int sr = 0, cpos = 0;   // stage within the row, stage within the chunk
         for (int st = 0; st < w.n_stages; ++st, ++s_g) {
           const int slot = (int)(s_g % STAGES);
-          const int buf = (int)(c_g % nbuf);
-          const int sr = st % spr;
-          const bool chunk_first = (sr % prm.chunk_stages) == 0;
-          const bool chunk_last = (sr % prm.chunk_stages) == prm.chunk_stages - 1 ||
-                                  sr == spr - 1;
+          const bool chunk_first = cpos == 0;
+          const bool chunk_last = cpos == prm.chunk_stages - 1 || sr == spr - 1;
+          if (++sr == spr) { sr = 0; cpos = 0; }
+          else if (++cpos == prm.chunk_stages) cpos = 0;
           // the chunk's accumulator buffer must have been drained (its previous use)
           if (chunk_first && c_g >= nbuf) {
-            if (!wait_bounded(smem_u32(&bar_acc_empty[buf]), (uint32_t)(((c_g / nbuf) + 1) & 1),
+            if (!wait_bounded(smem_u32(&bar_acc_empty[buf]), buf_par ^ 1u,
                               &abort_flag, prm.status, prm.wait_limit)) { stop = true; break; }
           }
           if (!wait_bounded(smem_u32(&bar_full[slot]), (uint32_t)((s_g / STAGES) & 1),
@@ -893,6 +897,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
           if (chunk_last) {
             tc_commit(smem_u32(&bar_acc_full[buf]));
             ++c_g;
+            if (++buf == nbuf) { buf = 0; buf_par ^= 1u; }
           }
         }
       }
@@ -917,24 +922,30 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const uint32_t run_r = tmem + lane_base + (uint32_t)(nbuf * 4 * NC);
     long long c_g = 0;
+    int buf = 0;              // c_g mod nbuf and the parity c_g / nbuf, kept incrementally
+    uint32_t buf_par = 0;
     for (long long u = u0; u < prm.total_units; u += du) {
       const Unit w = decode(u);
       const int spr = RF ? prm.rf_spr : w.n_stages;            // stages per chunk row
       const int cpr = (spr + prm.chunk_stages - 1) / prm.chunk_stages;
       const int n_chunks = (spr > 0 ? w.n_stages / spr : 0) * cpr;
-      for (int ch = 0; ch < n_chunks; ++ch, ++c_g) {
-        const int buf = (int)(c_g % nbuf);
+      int crow = 0, cin = 0;  // row-factored: the chunk's row in the unit, chunk in the row
+      auto next_chunk = [&] {
+        if (++buf == nbuf) { buf = 0; buf_par ^= 1u; }
+        if (++cin == cpr) { cin = 0; ++crow; }
+      };
+      for (int ch = 0; ch < n_chunks; ++ch, ++c_g, next_chunk()) {
         bool ok = !abort_flag;
         if (ok)
-          ok = wait_bounded(smem_u32(&bar_acc_full[buf]), (uint32_t)((c_g / nbuf) & 1),
-                            &abort_flag, prm.status, prm.wait_limit);
+          ok = wait_bounded(smem_u32(&bar_acc_full[buf]), buf_par, &abort_flag, prm.status,
+                            prm.wait_limit);
         // the TMEM loads below are warp-collective: decide per warp
         ok = __all_sync(0xffffffffu, ok);
-        if (RF && ch % cpr == 0) {
+        if (RF && cin == 0) {
           // row-factored, a new lattice row: its phase w^{n1 x1 + n2 x2} per momentum, once
           // per row, into shared memory. Every epilogue warp takes this step (whether or not
           // it drains), after the previous drain's barrier and before this row's reads.
-          const int lrow = w.x_begin + ch / cpr;
+          const int lrow = w.x_begin + crow;
           const int x1 = lrow % prm.L, x2 = lrow / prm.L;
           if (row < prm.P)
             s_rowph[row] = s_omega[(prm.rf_pn1[row] * x1 + prm.rf_pn2[row] * x2) % prm.L];
