@@ -11,6 +11,7 @@ constexpr int kMaxPairs = 16;   // distinct (alpha, beta) spin pairs
 // Row-factored tensor-core contraction: momenta per launch and distinct n0 values.
 constexpr int kMaxRfP = 16;
 constexpr int kMaxRfIdx = 8;
+constexpr int kMaxRfL = 128;    // lattice extent (the w^k table follows the stage buffers)
 // Momenta handled by one contraction launch of the FP64 form (10) and of the double-float
 // form (8): the largest counts whose accumulators fit the registers without spills.
 constexpr int kMaxPGroup = 10;

@@ -89,13 +89,16 @@ constexpr int kAPlaneBytes = kTcM * 96;          // 128 rows x 96 bytes of K per
 // the larger stages (less L1 for the producers' loads): it keeps two planes, Br | Bi, and
 // four MMAs of N = NC.
 // WIDE (the CTA-pair form): N tiles of up to kMaxNCWide complex columns, two stages.
-template <bool TF32, int LEVELS, bool F16 = false, bool WIDE = false> struct TcLayout {
+// TWO (the row-factored form): two stages of the narrow layout; the epilogue's row sums take
+// the third stage's room.
+template <bool TF32, int LEVELS, bool F16 = false, bool WIDE = false, bool TWO = false>
+struct TcLayout {
   static constexpr bool kTwoMma = TF32 || LEVELS == 3 || F16;
   static constexpr int kBPlanes = kTwoMma ? 3 : 2;
   static constexpr int kBr = kTwoMma ? 1 : 0, kBi = kBr + 1;   // plane slots; -Bi is slot 0
   static constexpr int kMaxCols = WIDE ? 80 : kMaxNC;          // complex columns per N tile
   static constexpr int kBPlaneB = kMaxCols * 96;               // bytes of one B plane
-  static constexpr int kStages = (LEVELS == 3 || WIDE) ? 2 : 3;
+  static constexpr int kStages = (LEVELS == 3 || WIDE || TWO) ? 2 : 3;
   static constexpr int kStageBytes = LEVELS * (2 * kAPlaneBytes + kBPlanes * kBPlaneB);
 };
 constexpr int kMaxNCWide = 80;
@@ -345,9 +348,9 @@ __device__ __forceinline__ Unit decode_unit_proj(const TcParams& prm, long long 
 //
 // RF (C = 1, the FP16 form): the row-factored phase. A chunk of MMAs never crosses a lattice
 // row; the B rows are (idx0, d3) with the factor w^{n0 x0} of the idx0-th distinct n0; the
-// epilogue adds each drained chunk, times the row's w^{n1 x1 + n2 x2}, into the running sum
-// of every momentum with that n0. The stages hold two stage buffers (the wide layout) and
-// the w table follows them in shared memory.
+// epilogue adds each drained chunk into the row's sums, and each complete row, times its
+// w^{n1 x1 + n2 x2}, into the running sum of every momentum with that n0. Two stage buffers
+// (N tiles of at most 48 columns), then the w table and the row sums in shared memory.
 template <bool TF32, int LEVELS, int NPROD, bool CHECKS, int C, bool PROJ, bool F16 = false,
           bool SHB = false, bool RF = false>
 __device__ __forceinline__ void tc_body(const TcParams& prm) {
@@ -362,7 +365,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   constexpr int G = TF32 ? 8 : 16;                 // (site, pair) groups per stage
   // transaction bytes a stage receives from the peers: their diquark rows, every plane
   constexpr uint32_t kPeerTx = (uint32_t)((C - 1) * (R::kARows / 8) * 768 * LEVELS * 2);
-  using Lay = TcLayout<TF32, LEVELS, F16, SHB || RF>;
+  using Lay = TcLayout<TF32, LEVELS, F16, SHB, RF>;
   constexpr int STAGES = Lay::kStages;
   constexpr int STAGE_BYTES = Lay::kStageBytes;
   constexpr bool kTwoMma = Lay::kTwoMma;   // complex product as two N = 2 NC MMAs
@@ -388,8 +391,9 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
   __shared__ const float2* s_q1[kMaxPairs];
   __shared__ const float2* s_q2[kMaxPairs];
   __shared__ const float2* s_q3[kMaxPairs];
-  // row-factored: the current lattice row's phase per momentum (epilogue)
-  __shared__ float2 s_rowph[kMaxRfP];
+  // row-factored: the phase per momentum of the current lattice row and of the previous one
+  // (epilogue; by row parity, so that a warp may start a row while another finishes the last)
+  __shared__ float2 s_rowph[2][kMaxRfP];
   __shared__ uint32_t s_rfmask[kMaxRfIdx];
 
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -414,8 +418,9 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // row-factored: the w^k table after the stage buffers
+  // row-factored: the w^k table after the stage buffers, then the row sums of the epilogue
   float2* s_omega = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);
+  float4* s_trow = reinterpret_cast<float4*>(smem + STAGES * STAGE_BYTES + kMaxRfL * sizeof(float2));
   if constexpr (RF) {
     for (int k = tid; k < prm.L; k += blockDim.x) s_omega[k] = prm.rf_omega[k];
     // the momenta of each distinct n0, as a bit mask
@@ -466,9 +471,13 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
       if (!kShareA) {
         rr = pt % kTcM;
         g0 = (pt / kTcM) * 8;
-      } else {   // 8 rows x 4 items per warp: the warp's rows are one core-matrix row group
-        rr = (int)rank * R::kARows + (pt / 32) * 8 + (lane >> 2);
-        g0 = (lane & 3) * 4;
+      } else {
+        // 8 rows x 4 runs of 4 groups per warp: the warp's rows are one core-matrix row group.
+        // Lanes 8q .. 8q + 7 take run q of the 8 rows, so that each half-warp's 8-byte stores
+        // fill one 128-byte core-matrix column (runs 0, 1: K bytes 0-15 of colour c; runs 2, 3:
+        // the next column) without bank conflicts.
+        rr = (int)rank * R::kARows + (pt / 32) * 8 + (lane & 7);
+        g0 = (lane >> 3) * 4;
       }
     } else {
       const int b = is_b ? pt - R::kAThreads : 0;
@@ -924,6 +933,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
     long long c_g = 0;
     int buf = 0;              // c_g mod nbuf and the parity c_g / nbuf, kept incrementally
     uint32_t buf_par = 0;
+    int rpar = 0;             // row-factored: parity of the rows taken so far (all units)
     for (long long u = u0; u < prm.total_units; u += du) {
       const Unit w = decode(u);
       const int spr = RF ? prm.rf_spr : w.n_stages;            // stages per chunk row
@@ -932,7 +942,7 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
       int crow = 0, cin = 0;  // row-factored: the chunk's row in the unit, chunk in the row
       auto next_chunk = [&] {
         if (++buf == nbuf) { buf = 0; buf_par ^= 1u; }
-        if (++cin == cpr) { cin = 0; ++crow; }
+        if (++cin == cpr) { cin = 0; ++crow; rpar ^= 1; }
       };
       for (int ch = 0; ch < n_chunks; ++ch, ++c_g, next_chunk()) {
         bool ok = !abort_flag;
@@ -941,90 +951,126 @@ __device__ __forceinline__ void tc_body(const TcParams& prm) {
                             prm.wait_limit);
         // the TMEM loads below are warp-collective: decide per warp
         ok = __all_sync(0xffffffffu, ok);
-        if (RF && cin == 0) {
-          // row-factored, a new lattice row: its phase w^{n1 x1 + n2 x2} per momentum, once
-          // per row, into shared memory. Every epilogue warp takes this step (whether or not
-          // it drains), after the previous drain's barrier and before this row's reads.
-          const int lrow = w.x_begin + crow;
-          const int x1 = lrow % prm.L, x2 = lrow / prm.L;
-          if (row < prm.P)
-            s_rowph[row] = s_omega[(prm.rf_pn1[row] * x1 + prm.rf_pn2[row] * x2) % prm.L];
-          __syncwarp();
-          named_bar(kBarEpi, kEpiWarps * 32);
-        }
-        if (ok && RF) {
-          // row-factored: chunk sums t = lead + corr of each n0 block, times the row's
-          // w^{n1 x1 + n2 x2}, into the running sum of every momentum with that n0
-          tc_fence_after();
-          const uint32_t lead = tmem + lane_base;
-          const int ncol = prm.rf_nc;
-          for (int i0 = 0; i0 < prm.rf_nidx; ++i0) {
-            const uint32_t msk = s_rfmask[i0];   // the momenta with this n0
-            for (int col = 0; col < ncol; col += 16) {
-              float tr[16], ti[16], cr[16], ci[16];
-              tmem_ld16(lead + i0 * ncol + col, tr);
-              tmem_ld16(lead + NC + i0 * ncol + col, ti);
-              tmem_ld16(lead + 2 * NC + i0 * ncol + col, cr);
-              tmem_ld16(lead + 3 * NC + i0 * ncol + col, ci);
+        if constexpr (RF) {
+          if (cin == 0) {
+            // a new lattice row: its phase w^{n1 x1 + n2 x2} per momentum, once per row, into
+            // the shared-memory slot of the row's parity. Every epilogue warp takes this step
+            // (whether or not it drains): a warp may still read the previous row's slot.
+            const int lrow = w.x_begin + crow;
+            const int x1 = lrow % prm.L, x2 = lrow / prm.L;
+            if (row < prm.P)
+              s_rowph[rpar][row] = s_omega[(prm.rf_pn1[row] * x1 + prm.rf_pn2[row] * x2) % prm.L];
+            __syncwarp();
+            named_bar(kBarEpi, kEpiWarps * 32);
+          }
+          // Row-factored: the chunk sums t = lead + corr of this lane's row are added into the
+          // row's sums in shared memory (float4 slots [column / 4][row], so that a warp's
+          // accesses are contiguous), 16 columns at a time, and the accumulator is handed back
+          // to the MMA thread. The running sums of the momenta take each row once, at its
+          // last chunk, while the tensor cores run the next.
+          float4* const trow = s_trow + row;
+          if (ok) {
+            tc_fence_after();
+            const uint32_t lead = tmem + lane_base;
+            for (int b = 0; 16 * b < NC; ++b) {
+              float a_r[16], a_i[16], c_r[16], c_i[16];
+              tmem_ld16(lead + 16 * b, a_r);
+              tmem_ld16(lead + NC + 16 * b, a_i);
+              tmem_ld16(lead + 2 * NC + 16 * b, c_r);
+              tmem_ld16(lead + 3 * NC + 16 * b, c_i);
               tmem_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 16; i += 2) {
-                const float2 r2 = __fadd2_rn(make_float2(tr[i], tr[i + 1]), make_float2(cr[i], cr[i + 1]));
-                const float2 i2 = __fadd2_rn(make_float2(ti[i], ti[i + 1]), make_float2(ci[i], ci[i + 1]));
-                tr[i] = r2.x; tr[i + 1] = r2.y;
-                ti[i] = i2.x; ti[i + 1] = i2.y;
-              }
-              // the momenta with this n0: run += ph x t, the row's phase from shared memory
-              for (uint32_t m2 = msk; m2 != 0u; m2 &= m2 - 1u) {
-                const int p = __ffs(m2) - 1;
-                const float2 ph = s_rowph[p];
-                const uint32_t rp = run_r + (uint32_t)(p * 2 * ncol + col);
-                float rr[16], ri[16];
-                if (ch > 0) {
-                  tmem_ld16(rp, rr);
-                  tmem_ld16(rp + ncol, ri);
-                  tmem_wait_ld();
+              for (int q = 0; q < 4; ++q) {
+                float4 vr = make_float4(a_r[4 * q] + c_r[4 * q], a_r[4 * q + 1] + c_r[4 * q + 1],
+                                        a_r[4 * q + 2] + c_r[4 * q + 2], a_r[4 * q + 3] + c_r[4 * q + 3]);
+                float4 vi = make_float4(a_i[4 * q] + c_i[4 * q], a_i[4 * q + 1] + c_i[4 * q + 1],
+                                        a_i[4 * q + 2] + c_i[4 * q + 2], a_i[4 * q + 3] + c_i[4 * q + 3]);
+                float4* const pr = trow + (size_t)(4 * b + q) * kTcM;
+                float4* const pi = trow + (size_t)(NC / 4 + 4 * b + q) * kTcM;
+                if (cin > 0) {
+                  const float4 o = *pr, oi = *pi;
+                  vr = make_float4(o.x + vr.x, o.y + vr.y, o.z + vr.z, o.w + vr.w);
+                  vi = make_float4(oi.x + vi.x, oi.y + vi.y, oi.z + vi.z, oi.w + vi.w);
                 }
-                // two adjacent columns per packed FMA (each lane rounds as fmaf):
-                //   re = ph.x tr - ph.y ti + re,   im = ph.x ti + ph.y tr + im
-                const float2 phx = make_float2(ph.x, ph.x), phy = make_float2(ph.y, ph.y);
-                const float2 nphy = make_float2(-ph.y, -ph.y);
-#pragma unroll
-                for (int i = 0; i < 16; i += 2) {
-                  const float2 a = ch > 0 ? make_float2(rr[i], rr[i + 1]) : make_float2(0.f, 0.f);
-                  const float2 b = ch > 0 ? make_float2(ri[i], ri[i + 1]) : make_float2(0.f, 0.f);
-                  const float2 t_r = make_float2(tr[i], tr[i + 1]);
-                  const float2 t_i = make_float2(ti[i], ti[i + 1]);
-                  const float2 re = __ffma2_rn(phx, t_r, __ffma2_rn(nphy, t_i, a));
-                  const float2 im = __ffma2_rn(phx, t_i, __ffma2_rn(phy, t_r, b));
-                  rr[i] = re.x; rr[i + 1] = re.y;
-                  ri[i] = im.x; ri[i + 1] = im.y;
-                }
-                tmem_st16(rp, rr);
-                tmem_st16(rp + ncol, ri);
+                *pr = vr;
+                *pi = vi;
               }
             }
           }
-          tmem_wait_st();
-        } else if (ok) {
-          tc_fence_after();
-          const uint32_t lead = tmem + lane_base + (uint32_t)(buf * 4 * NC);
-          for (int col = 0; col < 2 * NC; col += 16) {
-            float a[16], b[16], r[16];
-            tmem_ld16(lead + col, a);
-            tmem_ld16(lead + 2 * NC + col, b);
-            if (ch > 0) tmem_ld16(run_r + col, r);
-            tmem_wait_ld();
+          tc_fence_before();
+          __syncwarp();
+          named_bar(kBarEpi, kEpiWarps * 32);
+          if (tid == 0) mbar_arrive(smem_u32(&bar_acc_empty[buf]));
+          __syncwarp();
+          if (ok) {
+            if (cin == cpr - 1) {
+              // the row is complete: its sums times the row's w^{n1 x1 + n2 x2}, into the
+              // running sum of every momentum with that n0. Each 16-column block lies in one
+              // n0 block (the d3 tile is a multiple of 16).
+              const int ncol = prm.rf_nc;
+              for (int b = 0; 16 * b < NC; ++b) {
+                const int i0 = (16 * b) / ncol, col = 16 * b - i0 * ncol;
+                float t_re[16], t_im[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) r[i] = (ch > 0 ? r[i] : 0.f) + (a[i] + b[i]);
-            tmem_st16(run_r + col, r);
+                for (int q = 0; q < 4; ++q) {
+                  const float4 vr = trow[(size_t)(4 * b + q) * kTcM];
+                  const float4 vi = trow[(size_t)(NC / 4 + 4 * b + q) * kTcM];
+                  t_re[4 * q] = vr.x; t_re[4 * q + 1] = vr.y; t_re[4 * q + 2] = vr.z; t_re[4 * q + 3] = vr.w;
+                  t_im[4 * q] = vi.x; t_im[4 * q + 1] = vi.y; t_im[4 * q + 2] = vi.z; t_im[4 * q + 3] = vi.w;
+                }
+                for (uint32_t m2 = s_rfmask[i0]; m2 != 0u; m2 &= m2 - 1u) {
+                  const int p = __ffs(m2) - 1;
+                  const float2 ph = s_rowph[rpar][p];
+                  const uint32_t rp = run_r + (uint32_t)(p * 2 * ncol + col);
+                  float rr[16], ri[16];
+                  if (crow > 0) {
+                    tmem_ld16(rp, rr);
+                    tmem_ld16(rp + ncol, ri);
+                    tmem_wait_ld();
+                  }
+                  // two adjacent columns per packed FMA (each lane rounds as fmaf):
+                  //   re = ph.x tr - ph.y ti + re,   im = ph.x ti + ph.y tr + im
+                  const float2 phx = make_float2(ph.x, ph.x), phy = make_float2(ph.y, ph.y);
+                  const float2 nphy = make_float2(-ph.y, -ph.y);
+#pragma unroll
+                  for (int i = 0; i < 16; i += 2) {
+                    const float2 a = crow > 0 ? make_float2(rr[i], rr[i + 1]) : make_float2(0.f, 0.f);
+                    const float2 c = crow > 0 ? make_float2(ri[i], ri[i + 1]) : make_float2(0.f, 0.f);
+                    const float2 tr2 = make_float2(t_re[i], t_re[i + 1]);
+                    const float2 ti2 = make_float2(t_im[i], t_im[i + 1]);
+                    const float2 re = __ffma2_rn(phx, tr2, __ffma2_rn(nphy, ti2, a));
+                    const float2 im = __ffma2_rn(phx, ti2, __ffma2_rn(phy, tr2, c));
+                    rr[i] = re.x; rr[i + 1] = re.y;
+                    ri[i] = im.x; ri[i + 1] = im.y;
+                  }
+                  tmem_st16(rp, rr);
+                  tmem_st16(rp + ncol, ri);
+                }
+              }
+              tmem_wait_st();
+            }
           }
-          tmem_wait_st();
+        } else {
+          if (ok) {
+            tc_fence_after();
+            const uint32_t lead = tmem + lane_base + (uint32_t)(buf * 4 * NC);
+            for (int col = 0; col < 2 * NC; col += 16) {
+              float a[16], b[16], r[16];
+              tmem_ld16(lead + col, a);
+              tmem_ld16(lead + 2 * NC + col, b);
+              if (ch > 0) tmem_ld16(run_r + col, r);
+              tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 16; ++i) r[i] = (ch > 0 ? r[i] : 0.f) + (a[i] + b[i]);
+              tmem_st16(run_r + col, r);
+            }
+            tmem_wait_st();
+          }
+          tc_fence_before();
+          __syncwarp();
+          named_bar(kBarEpi, kEpiWarps * 32);
+          if (tid == 0) mbar_arrive(smem_u32(&bar_acc_empty[buf]));
         }
-        tc_fence_before();
-        __syncwarp();
-        named_bar(kBarEpi, kEpiWarps * 32);
-        if (tid == 0) mbar_arrive(smem_u32(&bar_acc_empty[buf]));
         __syncwarp();   // tcgen05.ld below is warp-aligned
         if (PROJ && ok && ch == n_chunks - 1) {
           // projection unit done: the running sum is the field's tile q[m][n]
@@ -1216,10 +1262,12 @@ cudaError_t launch_pair(const TcParams& prm, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// The row-factored FP16 contraction: one CTA per SM; the stages, then the w^k table.
+// The row-factored FP16 contraction: one CTA per SM; the stages, the w^k table, then the
+// epilogue's row sums (128 rows x 2 NC floats).
 cudaError_t launch_rows(const TcParams& prm, int cluster, int grid, cudaStream_t s) {
-  using Lay = TcLayout<false, 2, true, true>;
-  const size_t smem = (size_t)Lay::kStages * Lay::kStageBytes + 128 * sizeof(float2);
+  using Lay = TcLayout<false, 2, true, false, true>;
+  const size_t smem = (size_t)Lay::kStages * Lay::kStageBytes + kMaxRfL * sizeof(float2) +
+                      (size_t)kTcM * 2 * kMaxNC * sizeof(float);
   auto kern = cluster == 2 ? k_contract_tc_rows2 : k_contract_tc_rows;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1255,7 +1303,7 @@ cudaError_t launch_rows(const TcParams& prm, int cluster, int grid, cudaStream_t
 // phase (unchecked).
 cudaError_t launch_form_f16(const TcParams& prm, int cluster, int grid, cudaStream_t s) {
   if (prm.rf) {
-    if (prm.checks || (cluster != 1 && cluster != 2) || prm.share_b || prm.L < 1 || prm.L > 128 ||
+    if (prm.checks || (cluster != 1 && cluster != 2) || prm.share_b || prm.L < 1 || prm.L > kMaxRfL ||
         prm.rf_nidx < 1 || prm.rf_nidx > kMaxRfIdx || prm.P > kMaxRfP || prm.rf_spr < 1 ||
         prm.rf_nc < 16 || prm.rf_nc % 16 != 0 || prm.NC != prm.rf_nidx * prm.rf_nc ||
         4 * prm.NC + 2 * prm.P * prm.rf_nc > kTmemCols || !prm.rf_omega)
