@@ -130,8 +130,9 @@ cudaError_t timed_launch(bblock_ctx* c, int kind, cudaStream_t s, F&& launch) {
       a = b = nullptr;
     }
   }
+  const long long n0 = t_kernel_launches;
   cudaError_t e = launch();
-  c->last_launches++;
+  c->last_launches += (int)(t_kernel_launches - n0);   // a step may launch several kernels
   if (a && b) {
     if (cudaEventRecordWithFlags(b, s, rec_flags) == cudaSuccess) {
       (c->capturing ? c->graph_timed : c->timed).push_back({kind, a, b});

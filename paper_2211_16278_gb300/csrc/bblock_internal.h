@@ -24,6 +24,11 @@ inline int p_group_size(int n_mom, int max_group) {
 }
 constexpr int kThreads = 256;   // threads per CTA of the FP64 kernels
 
+// Kernel launches made by the calling host thread, counted at every launch site of the
+// library (a call's launch count is the difference across it).
+inline thread_local long long t_kernel_launches = 0;
+inline void note_launch() { ++t_kernel_launches; }
+
 // Device-side status bits (OR-ed into the context's status word).
 constexpr int kStatusBadJob = 1;
 constexpr int kStatusTimeout = 2;   // a bounded wait of the tensor-core kernel gave up

@@ -33,6 +33,7 @@ cudaError_t launch_canaries(uint32_t* const* d_list, int n, bool check, int* sta
   if (n == 0) return cudaSuccess;
   const int grid = n < 4096 ? n : 4096;
   k_canaries<<<grid, 64, 0, s>>>(d_list, n, check ? 1 : 0, status);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -92,6 +92,7 @@ cudaError_t na_launch(const NoallocParams& prm, int grid, cudaStream_t s) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_contract_fp64_noalloc<P, RN><<<grid, kThreads, smem, s>>>(prm);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -290,6 +291,7 @@ extern "C" int bblock_contract_noalloc(int L, const void* q1, const void* q2, co
     if (bx > 4096) bx = 4096;
     k_reduce_noalloc<<<(unsigned)bx, kThreads, 0, s>>>(job.partial, static_cast<double2*>(B_out),
                                                        (long long)per, base.n_slab);
+    note_launch();
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

@@ -222,6 +222,7 @@ cudaError_t launch_df_p(const ContractParams& prm, int grid, cudaStream_t s) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_contract_df<P, 2, RN><<<grid, kThreads, smem, s>>>(prm);
+  note_launch();
   return cudaGetLastError();
 }
 

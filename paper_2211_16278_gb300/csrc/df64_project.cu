@@ -153,6 +153,7 @@ cudaError_t launch_convert_df(const DfConvSeg* d_segs, int n_segs, long long max
     if (bx > 1024) bx = 1024;
     dim3 grid((unsigned)bx, ns);
     k_convert_df<<<grid, kThreads, 0, s>>>(d_segs + s0);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -166,6 +167,7 @@ cudaError_t launch_project_df(const ProjField* d_fields, int n_fields, int rows,
     const int nf = n_fields - f0 < 65535 ? n_fields - f0 : 65535;
     dim3 grid((rows + DBM - 1) / DBM, (max_nd + DBN - 1) / DBN, nf);
     k_project_df<<<grid, kThreads, 0, s>>>(d_fields + f0, rows, n_ev);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

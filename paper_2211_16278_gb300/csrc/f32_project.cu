@@ -163,6 +163,7 @@ cudaError_t launch_convert_f32(const F32ConvSeg* d_segs, int n_segs, long long m
     if (bx > 1024) bx = 1024;
     dim3 grid((unsigned)bx, ns);
     k_convert_f32<<<grid, kThreads, 0, s>>>(d_segs + s0);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -175,6 +176,7 @@ cudaError_t launch_project_f32(const ProjFieldF* d_fields, int n_fields, int row
   if (n_fields == 0 || rows == 0) return cudaSuccess;
   dim3 grid(n_fields, (rows + FBM - 1) / FBM, (max_nd + FBN - 1) / FBN);
   k_project_f32<<<grid, kThreads, 0, s>>>(d_fields, rows, n_ev, checks, dbg, status);
+  note_launch();
   return cudaGetLastError();
 }
 

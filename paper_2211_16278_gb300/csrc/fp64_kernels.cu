@@ -49,6 +49,7 @@ cudaError_t launch_phase_table(int L, int n_mom, const int* d_mom, double2* ph, 
   if (total == 0) return cudaSuccess;
   const int grid = (int)((total + kThreads - 1) / kThreads < 65536 ? (total + kThreads - 1) / kThreads : 65536);
   k_phase_table<<<grid, kThreads, 0, s>>>(L, n_mom, d_mom, ph, ph_f);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -147,6 +148,7 @@ cudaError_t launch_project_fp64(const ProjField* d_fields, int n_fields, int row
     const int nf = n_fields - f0 < 65535 ? n_fields - f0 : 65535;
     dim3 grid((rows + PBM - 1) / PBM, (max_nd + PBN - 1) / PBN, nf);
     k_project_fp64<<<grid, kThreads, 0, s>>>(d_fields + f0, rows, n_ev);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -190,6 +192,7 @@ static cudaError_t launch_contract_p(const ContractParams& prm, int grid, cudaSt
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_contract_fp64<P, 2, RN><<<grid, kThreads, smem, s>>>(prm);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -256,6 +259,7 @@ cudaError_t launch_reduce_slabs(const ContractJob* d_jobs, int n_jobs, int n_sla
   if (bx > 4096) bx = 4096;
   dim3 grid((unsigned)bx, n_jobs);
   k_reduce_slabs<<<grid, kThreads, 0, s>>>(d_jobs, n_slab, P_total);
+  note_launch();
   return cudaGetLastError();
 }
 

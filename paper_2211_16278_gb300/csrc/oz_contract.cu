@@ -800,6 +800,7 @@ cudaError_t launch_oz_c(const ContractParams& prm, int grid, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   if (C == 1) {
     kern<<<grid, R::kThreads, smem, s>>>(prm);
+    note_launch();
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -821,6 +822,7 @@ cudaError_t launch_oz_c(const ContractParams& prm, int grid, cudaStream_t s) {
   if (max_clusters < 1) return cudaErrorInvalidConfiguration;
   cfg.gridDim = dim3((unsigned)(C * std::min(grid, max_clusters)));
   e = cudaLaunchKernelEx(&cfg, kern, prm);
+  note_launch();
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -848,6 +850,7 @@ cudaError_t launch_oz_colmax(const OzMaxSeg* d_segs, int n_segs, int X, int site
   if (n_segs == 0) return cudaSuccess;
   dim3 grid((unsigned)((X + kColmaxSites - 1) / kColmaxSites), (unsigned)n_segs);
   k_oz_colmax<<<grid, 256, 0, s>>>(d_segs, X, sites_per_slab);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -855,6 +858,7 @@ cudaError_t launch_oz_rowmax(const ContractParams& prm, int max_m_tiles, cudaStr
   if (prm.n_jobs == 0 || max_m_tiles == 0) return cudaSuccess;
   dim3 grid((unsigned)((prm.X + kRowmaxSites - 1) / kRowmaxSites), (unsigned)(prm.n_jobs * max_m_tiles));
   k_oz_rowmax<<<grid, 128, 0, s>>>(prm, max_m_tiles);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -862,6 +866,7 @@ cudaError_t launch_phase_df(const double2* ph, float4* out, long long n, cudaStr
   if (n == 0) return cudaSuccess;
   const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
   k_phase_df<<<blocks, 256, 0, s>>>(ph, out, n);
+  note_launch();
   return cudaGetLastError();
 }
 

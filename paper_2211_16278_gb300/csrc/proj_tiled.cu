@@ -386,15 +386,18 @@ cudaError_t launch_project_tiled(const TiledProjParams& prm, int n_vs, int n_fts
                                  cudaStream_t s) {
   if (prm.total_units == 0) return cudaSuccess;
   k_tile_v<<<(unsigned)(n_vs * prm.m_tiles * prm.k_stages), 512, 0, s>>>(prm);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_tile_phi<<<(unsigned)(n_fts * prm.k_stages), 256, 0, s>>>(prm);
+  note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = (size_t)kPStages * kPStageBytes;
   e = cudaFuncSetAttribute(k_project_tt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_project_tt<<<grid, kPThreads, smem, s>>>(prm);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -1194,6 +1194,7 @@ cudaError_t launch_variant(const TcParams& prm, int grid, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   if (C == 1) {
     kern<<<grid, Roles<TF32, C>::kThreads, smem, s>>>(prm);
+    note_launch();
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -1216,6 +1217,7 @@ cudaError_t launch_variant(const TcParams& prm, int grid, cudaStream_t s) {
   const long long want = (grid + C - 1) / C;
   cfg.gridDim = dim3((unsigned)(C * (want < max_clusters ? want : max_clusters)));
   e = cudaLaunchKernelEx(&cfg, kern, prm);
+  note_launch();
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -1228,6 +1230,7 @@ cudaError_t launch_projection(const TcParams& prm, int grid, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, Roles<TF32, 1>::kThreads, smem, s>>>(prm);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -1258,6 +1261,7 @@ cudaError_t launch_pair(const TcParams& prm, int grid, cudaStream_t s) {
   const long long want = (grid + 1) / 2;
   cfg.gridDim = dim3((unsigned)(2 * (want < max_clusters ? want : max_clusters)));
   e = cudaLaunchKernelEx(&cfg, kern, prm);
+  note_launch();
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -1273,6 +1277,7 @@ cudaError_t launch_rows(const TcParams& prm, int cluster, int grid, cudaStream_t
   if (e != cudaSuccess) return e;
   if (cluster == 1) {
     kern<<<grid, Roles<false, 1>::kThreads, smem, s>>>(prm);
+    note_launch();
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -1294,6 +1299,7 @@ cudaError_t launch_rows(const TcParams& prm, int cluster, int grid, cudaStream_t
   const long long want = (grid + 1) / 2;
   cfg.gridDim = dim3((unsigned)(2 * (want < max_clusters ? want : max_clusters)));
   e = cudaLaunchKernelEx(&cfg, kern, prm);
+  note_launch();
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -1406,6 +1412,7 @@ cudaError_t launch_reduce_slabs_f32(const TcJob* d_jobs, int n_jobs, int n_slab,
   if (bx > 4096) bx = 4096;
   dim3 grid((unsigned)bx, n_jobs);
   k_reduce_slabs_f32<<<grid, kThreads, 0, s>>>(d_jobs, n_slab, P_total, checks, dbg, status);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -117,12 +117,14 @@ int grid_for(long long total) {
 
 cudaError_t launch_fill_identity(double2* id, int n_ev, cudaStream_t s) {
   k_fill_identity<<<grid_for(4LL * n_ev * n_ev), kThreads, 0, s>>>(id, n_ev);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_fold_phi(const double2* phi, int n_ev, int nd, const FoldTerms& terms,
                             double2* out, cudaStream_t s) {
   k_fold_phi<<<grid_for((long long)n_ev * nd), kThreads, 0, s>>>(phi, n_ev, nd, terms, out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -136,6 +138,7 @@ cudaError_t launch_zgemm(const ZgemmParams& p, cudaStream_t s) {
     q.batch = (int)(p.batch - b0 < 65535 ? p.batch - b0 : 65535);
     dim3 grid((p.M + ZBM - 1) / ZBM, (p.N + ZBN - 1) / ZBN, q.batch);
     k_zgemm<<<grid, kThreads, 0, s>>>(q);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
