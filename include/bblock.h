@@ -294,12 +294,13 @@ int bblock_set_option(bblock_ctx* ctx, int option, int value);
 /* Current value of an option (>= 0), or BBLOCK_ERR_INVALID_ARG. */
 int bblock_get_option(const bblock_ctx* ctx, int option);
 
-/* Per-kernel timing: while enabled, every launch of the library is bracketed by
- * two CUDA events recorded on the launching stream. */
+/* Per-step timing: while enabled, every step of the path ("project" is the tiling of V
+ * and of the fields plus the projection kernel) is bracketed by two CUDA events recorded
+ * on the launching stream. */
 typedef struct {
   char name[32];    /* "phase", "project", "contract", "reduce", ... */
-  int launches;     /* launches timed since the last read */
-  double total_ms;  /* summed event-to-event durations of those launches */
+  int launches;     /* kernel launches of the steps timed since the last read */
+  double total_ms;  /* summed event-to-event durations of those steps */
 } bblock_kernel_stat;
 
 /* Turn launch timing on (enable != 0) or off. Off by default. Every kernel launch is

@@ -56,7 +56,7 @@ struct bblock_ctx {
   // launch timing (bblock_profile_enable)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
-  struct Timed { int kind; cudaEvent_t a, b; };
+  struct Timed { int kind; cudaEvent_t a, b; int kernels; };   // one timed step, its kernels
   std::vector<Timed> timed;
   // launch timing of CUDA-graph replays: event pairs captured as event-record nodes of the
   // graph (owned while the graph lives); a replay re-records them, so their times are
@@ -135,7 +135,8 @@ cudaError_t timed_launch(bblock_ctx* c, int kind, cudaStream_t s, F&& launch) {
   c->last_launches += (int)(t_kernel_launches - n0);   // a step may launch several kernels
   if (a && b) {
     if (cudaEventRecordWithFlags(b, s, rec_flags) == cudaSuccess) {
-      (c->capturing ? c->graph_timed : c->timed).push_back({kind, a, b});
+      (c->capturing ? c->graph_timed : c->timed)
+          .push_back({kind, a, b, (int)(t_kernel_launches - n0)});
     } else {
       cudaGetLastError();
       c->ev_pool.push_back(a);
@@ -164,7 +165,7 @@ cudaError_t harvest_graph_times(bblock_ctx* c) {
       continue;
     }
     c->graph_ms[t.kind] += m;
-    c->graph_cnt[t.kind] += 1;
+    c->graph_cnt[t.kind] += t.kernels;
   }
   return rc;
 }
@@ -2253,7 +2254,7 @@ int bblock_profile_read(bblock_ctx* c, bblock_kernel_stat* out, int max_entries,
     if (e == cudaSuccess) e = cudaEventElapsedTime(&m, t.a, t.b);
     if (e != cudaSuccess && rc == BBLOCK_OK) rc = cuda_fail(c, e, "bblock_profile_read");
     ms[t.kind] += m;
-    cnt[t.kind] += 1;
+    cnt[t.kind] += t.kernels;
     c->ev_pool.push_back(t.a);
     c->ev_pool.push_back(t.b);
   }
