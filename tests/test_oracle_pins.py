@@ -176,6 +176,32 @@ def test_inverse_dft_recovers_site_determinants(L):
     assert rel(per_site, ref) < 1e-12
 
 
+@pytest.mark.parametrize("L", [3, 4])
+def test_row_factored_phase_reproduces_eq1(L):
+    """The reading behind the FP16 form's row-factored path: for integer momenta,
+    e^{-i p.x} = w^{n0 x0} w^{n1 x1 + n2 x2} with w = e^{-2 pi i / L}. Summing the site
+    singlets of each lattice row (x1, x2) against w^{n0 x0} once per distinct n0 (mod L),
+    then the rows against w^{n1 x1 + n2 x2}, gives Eq. (1) for every momentum, including
+    components beyond L and negative ones, and momenta that share their n0."""
+    mom = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+           (1, 1, 0), (-1, -1, 0), (L + 1, 2, -3)]
+    spins = [(0, 1, 0), (1, 0, 0), (2, 3, 2)]
+    coeffs = [0.5, -0.5, 0.3 + 0.2j]
+    V, phis, mom, spins, coeffs = random_case(L, 5, (3, 4, 2), mom, spins, coeffs, seed=41 + L)
+    B = oracle.bblock(L, V, *phis, mom, spins, coeffs)
+    S = site_dets(V, phis, spins, coeffs).reshape(L, L, L, 3, 4, 2)   # [x2][x1][x0][d1][d2][d3]
+    w = np.exp(-2j * np.pi / L)
+    k = np.arange(L)
+    # per lattice row, one sum per distinct n0
+    rows = {n0: np.einsum("k,abkdef->abdef", w ** ((n0 * k) % L), S)
+            for n0 in sorted({int(m[0]) % L for m in mom})}
+    assert len(rows) < len(mom)
+    x1, x2 = k[None, :], k[:, None]
+    got = np.stack([np.einsum("ab,abdef->def", w ** ((int(n1) * x1 + int(n2) * x2) % L),
+                              rows[int(n0) % L]) for n0, n1, n2 in mom])
+    assert rel(got, B) < 1e-12
+
+
 # ---------------------------------------------------------------- I3 antisymmetry
 
 def _case_c1_like(seed, nd=(4, 5, 3), L=2, n_ev=5):
