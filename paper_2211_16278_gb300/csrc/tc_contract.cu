@@ -1,5 +1,6 @@
 // Tensor-core forms of the fused diquark + contraction (Eq. 1/3) on sm_103a: tcgen05 MMAs
-// with FP32 accumulators in tensor memory (TMEM), operands split into BF16 or TF32 pieces.
+// with FP32 accumulators in tensor memory (TMEM), operands split into BF16, TF32 or FP16
+// pieces.
 //
 // The contraction is a complex GEMM per (time slice, noise triple):
 //   C[(d1,d2)][(p,d3)] += sum_k A[(d1,d2)][k] * Bop[k][(p,d3)],   k = (site, spin pair, colour)
@@ -19,6 +20,14 @@
 // running sum (round to nearest) kept in TMEM; the smaller correction products share a
 // second accumulator. Each work unit (job, 128 pairs, NC columns, site slab) writes its
 // running sum as an FP32 partial block; the slab partials are summed in FP64 in index order.
+//
+// The FP16 form (two pieces per operand, scaled per job by powers of two) has two faster
+// variants: CTA pairs sharing the third-quark tile, and the row-factored phase, which
+// multiplies the third quark by w^{n0 x0} for each distinct x-component n0 of the momenta
+// only (w = e^{-2 pi i / L}) and applies w^{n1 x1 + n2 x2} per lattice row in the epilogue;
+// there the drained chunks are summed per row in shared memory and each complete row goes
+// into the running sum of every momentum (the batched workload's default, in clusters of two
+// CTAs that share the diquark tile; details before tc_body).
 //
 // Clusters (BF16 forms): C CTAs of a thread-block cluster take the same (job, 128 pairs,
 // slab) and C neighbouring N tiles. Each builds only 128/C rows of the diquark tile and
