@@ -121,6 +121,9 @@ def parse_args(argv=None):
                     "fp64 for the others)" % BATCH_HEAD)
     ap.add_argument("--n-t", type=int, default=None,
                     help="time slices per step (default: the workload's); for profiling runs")
+    ap.add_argument("--size-sweep", action="store_true",
+                    help="instead of the throughput line: the contraction time's growth with "
+                    "L and with N_dil (one JSON line)")
     return ap.parse_args(argv)
 
 
@@ -1145,10 +1148,72 @@ def run_ours(args):
     return 0
 
 
+SWEEP_N_EV = 96
+SWEEP_POINTS = [(16, 32), (24, 32), (32, 32), (48, 32), (32, 16), (32, 48), (32, 64)]
+
+
+def loglog_slope(xs, ys):
+    """Least-squares slope of log y against log x."""
+    lx = [math.log(x) for x in xs]
+    ly = [math.log(y) for y in ys]
+    mx, my = statistics.fmean(lx), statistics.fmean(ly)
+    return sum((a - mx) * (b - my) for a, b in zip(lx, ly)) / sum((a - mx) ** 2 for a in lx)
+
+
+def run_size_sweep(args):
+    """Problem-size scaling of the contraction (the paper's observation, Sec. 4, that its
+    time grows as L^3 and as N_dil^3): one time slice of the 9-momentum, 4-triple operator of
+    the batched workload, N_ev = 96, for L in {16, 24, 32, 48} at N_dil = 32 and for N_dil in
+    {16, 32, 48, 64} at L = 32, in the FP16 form and the FP64 form. Contraction time per call
+    from CUDA events (3 warm-up, 3 timed graph replays); exponents fitted on log-log."""
+    import torch
+
+    import paper_2211_16278_gb300 as bb
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    R = Runner(torch, bb, dev, 0, 1, lambda: None, torch.cuda.Stream(dev))
+    mom = workloads.MOM_C4
+    spins, coeffs = workloads.SPIN_C3
+    points = []
+    for i, (L, D) in enumerate(SWEEP_POINTS):
+        inp = workloads.custom(L, SWEEP_N_EV, (D, D, D), 1, mom, spins, coeffs, seed=9000 + i)
+        V = torch.from_numpy(inp.V).to(dev)
+        phis = [torch.from_numpy(inp.phi[0][k]).to(dev) for k in range(3)]
+        for form in ("fp16x3", "fp64"):
+            precision, products = FORMS[form][:2]
+            ctx = bb.bblock_create(L, SWEEP_N_EV, D, precision, bf16_products=products)
+            B = torch.empty((1, len(mom), D, D, D), dtype=torch.complex128, device=dev)
+
+            def step():
+                bb.bblock_compute(ctx, V, *phis, inp.momenta, inp.spins, inp.coeffs, B_out=B,
+                                  stream=R.stream)
+            t_ms, prof, _ = R.measure(ctx, step, 3, 3)
+            points.append({"L": L, "n_dil": D, "form": form, "path": bb.bblock_last_path(ctx),
+                           "contract_ms": prof["contract"][1] / 3, "call_ms": t_ms / 3})
+            bb.bblock_destroy(ctx)
+    fits = {}
+    for form in ("fp16x3", "fp64"):
+        lp = [p for p in points if p["form"] == form and p["n_dil"] == 32]
+        dp = [p for p in points if p["form"] == form and p["L"] == 32]
+        fits[form] = {
+            "L_exponent": loglog_slope([p["L"] for p in lp], [p["contract_ms"] for p in lp]),
+            "n_dil_exponent": loglog_slope([p["n_dil"] for p in dp], [p["contract_ms"] for p in dp]),
+        }
+    print(json.dumps({"size_sweep": {"n_ev": SWEEP_N_EV, "momenta": len(mom),
+                                     "spin_triples": len(spins), "time_slices": 1,
+                                     "points": points, "fits": fits,
+                                     "expected": "exponent 3 in L (sites) and in N_dil"}}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.size_sweep:
+        return run_size_sweep(args)
     return run_ours(args)
 
 
