@@ -42,3 +42,16 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_size_sweep_fit_recovers_power_laws():
+    """The size sweep's exponent fit (least squares on log-log) returns the power of an exact
+    power law, and the sweep's points span both series it fits."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for k in (2.0, 3.0):
+        assert abs(bench.loglog_slope([16, 24, 32, 48], [7.0 * L ** k for L in (16, 24, 32, 48)]) - k) < 1e-12
+    assert bench.parse_args(["--size-sweep"]).size_sweep
+    Ls = sorted({L for L, D in bench.SWEEP_POINTS if D == 32})
+    Ds = sorted({D for L, D in bench.SWEEP_POINTS if L == 32})
+    assert len(Ls) >= 3 and len(Ds) >= 3
